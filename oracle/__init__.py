@@ -1,0 +1,139 @@
+"""The oracle -- TEST INFRASTRUCTURE ONLY.
+
+A ctypes wrapper around ``ba_oracle.c``, the plain single-threaded CPU statement of the
+Batagelj-Brandes edge array (Sanders & Schulz, arXiv:1602.07106, section 2; seed graph
+of section 4).  Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package.  It shares no code with the CUDA library.
+
+Every function returns numpy arrays; nothing here touches a GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ba_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+
+_lib = None
+_lock = threading.Lock()
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_ptr = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile ``ba_oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared", "-fPIC",
+                    "-o", tmp, _SRC], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.ora_hash_bits.restype = _u64
+        lib.ora_hash_bits.argtypes = [_u64, _u64]
+        lib.ora_hash.restype = _u64
+        lib.ora_hash.argtypes = [_u64, _u64]
+        lib.ora_num_edges.restype = _u64
+        lib.ora_num_edges.argtypes = [_u64, _u32, _u64]
+        lib.ora_bb_array.restype = ctypes.c_int
+        lib.ora_bb_array.argtypes = [_u64, _u64, _u32, _u64, _ptr]
+        for name in ("ora_edges_range", "ora_chain_lengths"):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = [_u64, _u64, _u32, _u64, _u64, _u64, _ptr]
+        lib.ora_degrees_of_array.restype = None
+        lib.ora_degrees_of_array.argtypes = [_ptr, _u64, _u64, _ptr]
+        lib.ora_degree_count_range.restype = ctypes.c_int
+        lib.ora_degree_count_range.argtypes = [_u64, _u64, _u32, _u64, _u64, _u64, _u64,
+                                               _ptr]
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def hash_bits(seed: int, r: int) -> int:
+    """The 64 mixed bits z for position r (before reduction to 0..r-1)."""
+    return int(_load().ora_hash_bits(seed, r))
+
+
+def h(seed: int, r: int) -> int:
+    """h(r) in 0..r-1 (section 2)."""
+    return int(_load().ora_hash(seed, r))
+
+
+def num_edges(n: int, d: int, n0: int = 0) -> int:
+    """m = n0(n0-1)/2 + (n-n0) d; 0 when the parameters are not a graph."""
+    return int(_load().ora_num_edges(n, d, n0))
+
+
+def seed_edges(n0: int) -> int:
+    return n0 * (n0 - 1) // 2 if n0 > 0 else 0
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what}: invalid graph parameters or range")
+
+
+def bb_array(seed: int, n: int, d: int, n0: int = 0) -> np.ndarray:
+    """The full Batagelj-Brandes array E[0..2m-1] (int64)."""
+    m = num_edges(n, d, n0)
+    if m == 0:
+        raise ValueError("oracle bb_array: invalid graph parameters")
+    E = np.empty(2 * m, dtype=np.int64)
+    _check(_load().ora_bb_array(seed, n, d, n0, _p(E)), "bb_array")
+    return E
+
+
+def edges_range(seed: int, n: int, d: int, n0: int, a: int, b: int) -> np.ndarray:
+    """Edges a..b-1 as an int64 array of shape (b-a, 2), recomputed without the array."""
+    out = np.empty((max(b - a, 0), 2), dtype=np.int64)
+    _check(_load().ora_edges_range(seed, n, d, n0, a, b, _p(out)), "edges_range")
+    return out
+
+
+def chain_lengths(seed: int, n: int, d: int, n0: int, a: int, b: int) -> np.ndarray:
+    """Hash evaluations spent on the second end point of each edge a..b-1."""
+    out = np.empty(max(b - a, 0), dtype=np.uint64)
+    _check(_load().ora_chain_lengths(seed, n, d, n0, a, b, _p(out)), "chain_lengths")
+    return out
+
+
+def degrees_of_array(E: np.ndarray, node_limit: int) -> np.ndarray:
+    E = np.ascontiguousarray(E, dtype=np.int64)
+    counts = np.zeros(node_limit, dtype=np.uint64)
+    _load().ora_degrees_of_array(_p(E), E.size, node_limit, _p(counts))
+    return counts
+
+
+def degree_count_range(seed: int, n: int, d: int, n0: int, a: int, b: int,
+                       node_limit: int, counts: np.ndarray | None = None) -> np.ndarray:
+    """Degrees (end-point occurrences) of nodes 0..node_limit-1 over edges a..b-1."""
+    if counts is None:
+        counts = np.zeros(node_limit, dtype=np.uint64)
+    assert counts.dtype == np.uint64 and counts.size == node_limit
+    _check(_load().ora_degree_count_range(seed, n, d, n0, a, b, node_limit, _p(counts)),
+           "degree_count_range")
+    return counts

@@ -1,0 +1,204 @@
+/*
+ * ba_oracle.c -- TEST INFRASTRUCTURE ONLY (the oracle).
+ *
+ * A plain, slow, single-threaded CPU statement of the Barabasi-Albert edge array of
+ * Sanders & Schulz, "Scalable Generation of Scale-free Graphs" (arXiv:1602.07106).
+ * Only the test-suite, the benchmark's CPU-baseline leg and the smoke check call it;
+ * the library's product path never does.  It shares no code, header, table or constant
+ * generator with the CUDA library: every line here is written from the paper's
+ * definitions, with no blocking, fusion or reordering.
+ *
+ * What it computes (paper section 2, the Batagelj-Brandes edge array E):
+ *   E[0 .. 2m-1], positions 2i and 2i+1 hold the two end points of edge i.
+ *   E[2i]   = the node that edge i belongs to (floor(i/d) for an empty seed graph),
+ *   E[2i+1] = E[x], x drawn uniformly from 0..2i by the hash h(2i+1).
+ * Section 4 (seed graph): the first m0 edges are the seed network; here it is the clique
+ * on nodes 0..n0-1, m0 = n0(n0-1)/2, listed v = 1..n0-1, u = 0..v-1 as edge (v, u).
+ * Node n0 + j (j >= 0) then owns edges m0 + j*d .. m0 + (j+1)*d - 1.
+ *
+ * h(r) (section 2 asks for "a hash function mapping r to a random number in 0..r-1"):
+ *   z = SplitMix64 finaliser (Steele, Lea & Flood 2014; Stafford's "Mix13") of
+ *       seed XOR (r * 0x9E3779B97F4A7C15 mod 2^64),
+ *   h = floor(z * r / 2^64)   (Lemire's multiply-shift reduction to 0..r-1).
+ *
+ * Errors: every entry point returns 0 on success and a negative value when the
+ * parameters do not describe a graph (d = 0, n0 > n, n = 0, 2m + 1 >= 2^64, or an
+ * edge range outside 0..m).  Buffers belong to the caller.
+ */
+#include <stdint.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+#define ORA_GOLDEN_GAMMA 0x9E3779B97F4A7C15ULL
+
+/* ------------------------------------------------------------------ the hash h(r) -- */
+
+/* SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014). */
+static uint64_t splitmix64_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return z;
+}
+
+/* The 64 pseudo-random bits drawn for array position r (before range reduction). */
+uint64_t ora_hash_bits(uint64_t seed, uint64_t r)
+{
+    uint64_t x = seed ^ (r * ORA_GOLDEN_GAMMA);
+    return splitmix64_mix(x);
+}
+
+/* h(r) in 0..r-1 (section 2): the high 64 bits of the 128-bit product z * r. */
+uint64_t ora_hash(uint64_t seed, uint64_t r)
+{
+    u128 product = (u128)ora_hash_bits(seed, r) * (u128)r;
+    return (uint64_t)(product >> 64);
+}
+
+/* ------------------------------------------------------------ graph parameters -- */
+
+/* Seed-clique edge count m0 = n0(n0-1)/2 (section 4). */
+static u128 seed_edges(uint64_t n0)
+{
+    if (n0 == 0) return 0;
+    return ((u128)n0 * (u128)(n0 - 1)) / 2;
+}
+
+/* m = m0 + (n - n0) d, or 0 when (n, d, n0) is not a graph or 2m + 1 overflows 64 bits. */
+uint64_t ora_num_edges(uint64_t n, uint32_t d, uint64_t n0)
+{
+    if (n == 0 || d == 0 || n0 > n) return 0;
+    u128 m = seed_edges(n0) + (u128)(n - n0) * (u128)d;
+    if (m > ((u128)1 << 62)) return 0;
+    return (uint64_t)m;
+}
+
+/* ------------------------------------------------------ the edge array E (section 2) -- */
+
+/* Value of the seed-clique position p < 2 m0: edge k = p/2 is (v, u) with
+ * k = v(v-1)/2 + u, 0 <= u < v; E[2k] = v, E[2k+1] = u.  Found by walking v upwards. */
+static int64_t seed_clique_position(uint64_t p)
+{
+    uint64_t k = p / 2;
+    uint64_t v = 1;
+    uint64_t first = 0;              /* index of edge (v, 0) */
+    while (first + v <= k) {         /* edges (v, 0..v-1) are first .. first+v-1 */
+        first += v;
+        v += 1;
+    }
+    uint64_t u = k - first;
+    return (p % 2 == 0) ? (int64_t)v : (int64_t)u;
+}
+
+/*
+ * The Batagelj-Brandes array, written out in full (section 2 and section 4):
+ *   E[0 .. 2m0-1] = the seed clique,
+ *   for i = m0 .. m-1:  E[2i] = n0 + floor((i - m0)/d);  E[2i+1] = E[h(2i+1)].
+ * E must hold 2m int64 values.
+ */
+int ora_bb_array(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, int64_t *E)
+{
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (m == 0) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+
+    uint64_t p = 0;
+    for (uint64_t v = 1; v < n0; v++) {
+        for (uint64_t u = 0; u < v; u++) {
+            E[p] = (int64_t)v;
+            E[p + 1] = (int64_t)u;
+            p += 2;
+        }
+    }
+    for (uint64_t i = m0; i < m; i++) {
+        E[2 * i] = (int64_t)(n0 + (i - m0) / d);
+        uint64_t x = ora_hash(seed, 2 * i + 1);   /* uniform in 0..2i */
+        E[2 * i + 1] = E[x];
+    }
+    return 0;
+}
+
+/*
+ * E[p] from the same definition, without the array: a seed position is looked up, an
+ * even position 2j is the owner of edge j, and an odd position q >= 2 m0 holds whatever
+ * E[h(q)] holds, so the definition is followed until it reaches one of the first two.
+ * This is the recomputation argument of section 2 (Fig. 1 with the section 4 seed graph).
+ * *steps (may be NULL) receives the number of hash evaluations, the work counted in the
+ * section 2 bound.
+ */
+static int64_t position_value(uint64_t seed, uint32_t d, uint64_t n0, uint64_t m0,
+                              uint64_t p, uint64_t *steps)
+{
+    uint64_t count = 0;
+    for (;;) {
+        if (p < 2 * m0) {
+            if (steps) *steps = count;
+            return seed_clique_position(p);
+        }
+        if (p % 2 == 0) {
+            if (steps) *steps = count;
+            return (int64_t)(n0 + (p / 2 - m0) / d);
+        }
+        p = ora_hash(seed, p);
+        count += 1;
+    }
+}
+
+/* Edges a..b-1 as (E[2i], E[2i+1]) pairs into out[2(b-a)], by the recomputation above. */
+int ora_edges_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                    uint64_t a, uint64_t b, int64_t *out)
+{
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (m == 0 || a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    for (uint64_t i = a; i < b; i++) {
+        out[2 * (i - a)] = position_value(seed, d, n0, m0, 2 * i, NULL);
+        out[2 * (i - a) + 1] = position_value(seed, d, n0, m0, 2 * i + 1, NULL);
+    }
+    return 0;
+}
+
+/* Number of hash evaluations needed for the second end point of each edge a..b-1. */
+int ora_chain_lengths(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                      uint64_t a, uint64_t b, uint64_t *len)
+{
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (m == 0 || a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    for (uint64_t i = a; i < b; i++) {
+        uint64_t steps = 0;
+        position_value(seed, d, n0, m0, 2 * i + 1, &steps);
+        len[i - a] = steps;
+    }
+    return 0;
+}
+
+/* ----------------------------------------------------------- degrees (section 3) -- */
+
+/* counts[j] += number of positions p < len with E[p] == j, for j < node_limit. */
+void ora_degrees_of_array(const int64_t *E, uint64_t len, uint64_t node_limit,
+                          uint64_t *counts)
+{
+    for (uint64_t p = 0; p < len; p++) {
+        if ((uint64_t)E[p] < node_limit) counts[E[p]] += 1;
+    }
+}
+
+/* counts[j] += number of end points equal to j among edges a..b-1 (a self-loop counts
+ * twice), for j < node_limit; the streaming degree analysis of section 3. */
+int ora_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                           uint64_t a, uint64_t b, uint64_t node_limit, uint64_t *counts)
+{
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (m == 0 || a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    for (uint64_t i = a; i < b; i++) {
+        uint64_t u = (uint64_t)position_value(seed, d, n0, m0, 2 * i, NULL);
+        uint64_t v = (uint64_t)position_value(seed, d, n0, m0, 2 * i + 1, NULL);
+        if (u < node_limit) counts[u] += 1;
+        if (v < node_limit) counts[v] += 1;
+    }
+    return 0;
+}
