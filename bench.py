@@ -1,0 +1,525 @@
+#!/usr/bin/env python3
+"""Benchmark of the Barabasi-Albert edge generator (Sanders & Schulz, arXiv:1602.07106).
+
+One step = the whole hot path over the large plain workload (n = 2^27, d = 16, seed 42,
+m = 2^31 edges): ba_generate_edges writes all 2^31 edges to HBM as int64 pairs (34.4 GB)
+and ba_degree_count streams the same 2^31 edges into the degree histogram of nodes
+0..99,999 (section 3's analysis, no storage).  `value` counts edge generations per second
+(2 x 2^31 per step per GPU).  Under torchrun each rank takes its own 2^31-edge slice of a
+graph N times larger (contiguous edge ranges, no exchange) and the degree counts are
+summed across ranks.
+
+Extra keys: the streaming-only workload (n = 10^10, d = 100, 10^12 edges), the batched
+launch over the first wave of the 4096-graph table, the serving loop under Poisson
+arrivals, and the small workload (n = 10^6, d = 4).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1602_07106_gb300 import workloads as W  # noqa: E402
+
+NODE_LIMIT = W.DEGREE_NODE_LIMIT
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT_NOMINAL = 152
+SMSP_PER_SM = 4
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-extras", action="store_true", help="main step only")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-sample-edges", type=int, default=2**25)
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        # nvidia-smi numbers GPUs differently from CUDA under CUDA_VISIBLE_DEVICES: use the UUID
+        self.gpu = str(gpu_index)
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(gpu_index).uuid)
+            self.gpu = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis:
+                self.gpu = vis.split(",")[gpu_index]
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.file if ln.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- reference arm --
+
+def reference_arm(args):
+    """The oracle (plain single-threaded C per process) on the host cores over a bounded
+    sample of the same workload, one process per core."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import multiprocessing as mp
+
+    import oracle
+    from oracle import parallel as opar
+    oracle.build()
+    g = W.PLAIN_LARGE
+    cores = opar.default_workers()
+    sample = max(args.cpu_sample_edges // 4, 2**20)
+    pool = mp.get_context("spawn").Pool(cores)
+    try:
+        def one_step():
+            jobs_e = [(g.seed, g.n, g.d, 0, a, b) for a, b in opar._cuts(0, sample, cores)]
+            jobs_d = [(g.seed, g.n, g.d, 0, a, b, NODE_LIMIT) for a, b in opar._cuts(0, sample, cores)]
+            pool.map(opar._edges_piece, jobs_e)
+            pool.map(opar._degrees_piece, jobs_d)
+        for _ in range(args.warmup):
+            one_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step()
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    value = 2 * sample * args.steps / dt
+    line = {
+        "impl": "reference",
+        "metric": "edge generations/s (2^31-edge BA graph n=2^27 d=16: stored edge list + "
+                  "streamed degree count of nodes < 1e5)",
+        "value": value, "unit": "edges/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "plain BA n=2^27 d=16 seed=42 (sampled)",
+                   "sample_edges_per_step": 2 * sample},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
+                         "sample": f"edges [0, {sample}) generated and degree-counted per step"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
+    """Oracle timing on the host cores for the cpu_baseline key (rank 0, N = 1)."""
+    import multiprocessing as mp
+
+    import oracle
+    from oracle import parallel as opar
+    oracle.build()
+    g = W.PLAIN_LARGE
+    cores = opar.default_workers()
+    jobs_e = [(g.seed, g.n, g.d, 0, a, b) for a, b in opar._cuts(0, sample_edges, 4 * cores)]
+    jobs_d = [(g.seed, g.n, g.d, 0, a, b, NODE_LIMIT) for a, b in opar._cuts(0, sample_edges, 4 * cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(opar._edges_piece, jobs_e[:cores])      # start-up outside the timing
+        t0 = time.perf_counter()
+        pool.map(opar._edges_piece, jobs_e)
+        pool.map(opar._degrees_piece, jobs_d)
+        dt = time.perf_counter() - t0
+    return {"value": 2 * sample_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": f"edges [0, {sample_edges}) of n=2^27 d=16 seed=42: edge list + degree "
+                      f"count of nodes < 1e5, {dt:.1f} s wall on {cores} processes"}
+
+
+# ---------------------------------------------------------------------- GPU arm --
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_07106_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per edge from a committed ncu summary, if the kernels have not changed
+    since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_digest") != source_digest():
+        return None
+    return ent.get("dram_bytes_per_edge")
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1602_07106_gb300 import build as ba_build
+    ba_build.build()
+    from paper_1602_07106_gb300 import ba
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev_index = torch.cuda.current_device()
+    g = W.PLAIN_LARGE
+    m_shard = g.m
+    n_total = g.n * world
+    a0, a1 = rank * m_shard, (rank + 1) * m_shard
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = measured_peaks()
+
+    out = torch.empty((m_shard, 2), dtype=torch.int64, device="cuda")
+    counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        ba.ba_generate_edges(g.seed, n_total, g.d, 0, a0, a1, out, stream)
+        if ev:
+            ev[1].record(stream)
+        ba.ba_degree_count_range(g.seed, n_total, g.d, 0, a0, a1, NODE_LIMIT, counts, 0, stream)
+        if ev:
+            ev[2].record(stream)
+        if world > 1:
+            dist.all_reduce(counts)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    gen_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    deg_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    launches = args.steps * 3  # generate kernel + degree init + degree chain kernel
+    edges_per_step = 2 * m_shard * world
+    value = edges_per_step * args.steps / (elapsed_ms / 1e3)
+
+    gen_avg = statistics.mean(gen_ms) / 1e3
+    deg_avg = statistics.mean(deg_ms) / 1e3
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    gen_bytes = 16 * m_shard
+    gen_traffic = recorded_traffic("k_generate_refill")
+    roof_gen = {"kernel": "k_generate_refill", "bound": "hbm",
+                "achieved": gen_bytes / gen_avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gen_bytes / gen_avg / 1e9 / hbm_peak,
+                "traffic": gen_traffic * m_shard if gen_traffic is not None else None,
+                "peak_source": f"hbm_gbs of {peak_kind} (MEASURED_PEAKS.json copy bandwidth)",
+                "algorithmic_bytes_per_edge": 16, "ms": gen_avg * 1e3}
+    # ALU roofline of the degree count: 1 warp instruction per SMSP per clock at the
+    # maximum SM clock, against the algorithmic instruction count per edge of the 32-bit
+    # position path (hash 24 + stop test 1 per hash, 2.0 hashes per edge, 2 per edge for
+    # the hit test).
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    alu_peak = sms * SMSP_PER_SM * 32 * sm_max * 1e6 / 1e12      # tera thread-instr/s
+    instr_per_edge = 2.0 * 25 + 2
+    deg_achieved = instr_per_edge * m_shard / deg_avg / 1e12
+    deg_traffic = recorded_traffic("k_degree_refill")
+    roof_deg = {"kernel": "k_degree_refill", "bound": "alu", "achieved": deg_achieved,
+                "peak": alu_peak, "unit": "Tinstr/s", "frac": deg_achieved / alu_peak,
+                "traffic": deg_traffic * m_shard if deg_traffic is not None else None,
+                "peak_source": f"{sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
+                "algorithmic_instr_per_edge": instr_per_edge, "ms": deg_avg * 1e3}
+    dominant = roof_gen if gen_avg >= deg_avg else roof_deg
+
+    result = {
+        "metric": "edge generations/s (2^31-edge BA graph n=2^27 d=16: stored edge list + "
+                  "streamed degree count of nodes < 1e5)",
+        "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "plain BA n=2^27 d=16 seed=42, m=2^31 edges per GPU "
+                               "(edge list 34.4 GB in HBM + degree count of nodes < 1e5)",
+                   "edges_per_step": edges_per_step, "l2": "working set 34.4 GB > L2, no flush",
+                   "parallelism": f"edge-range shards x{world}"},
+        "roofline": dominant,
+        "roofline_kernels": [roof_gen, roof_deg],
+        "clocks": clk,
+        "gpu_launches": launches,
+        "kernels_ms": {"generate": gen_avg * 1e3, "degree": deg_avg * 1e3},
+    }
+
+    # ---- end to end through the C ABI with host buffers (rank-local) -------------
+    e2e = None
+    if args.e2e_steps > 0:
+        try:
+            host_out = torch.empty((m_shard, 2), dtype=torch.int64, pin_memory=True)
+            pinned = True
+        except RuntimeError:
+            host_out = torch.empty((m_shard, 2), dtype=torch.int64)
+            pinned = False
+        host_counts = torch.empty(NODE_LIMIT, dtype=torch.int64, pin_memory=pinned)
+
+        def e2e_step():
+            ba.ba_generate_edges_host(g.seed, n_total, g.d, 0, a0, a1, host_out, stream)
+            ba.ba_degree_count_range(g.seed, n_total, g.d, 0, a0, a1, NODE_LIMIT, counts, 0, stream)
+            if world > 1:
+                dist.all_reduce(counts)
+            host_counts.copy_(counts, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": edges_per_step * args.e2e_steps / dt, "unit": "edges/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 16 * m_shard + 8 * NODE_LIMIT,
+               "host_buffer": "pinned" if pinned else "pageable", "steps": args.e2e_steps,
+               "ms_per_step": 1000 * dt / args.e2e_steps}
+        del host_out
+    result["e2e"] = e2e
+
+    if not args.no_extras and world == 1:
+        del out
+        torch.cuda.empty_cache()
+        result["extras"] = extras(args, ba, torch, stream, result)
+
+    if rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline_leg(20.0, args.cpu_sample_edges)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time_events(fn, stream, torch, reps):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return ts
+
+
+def extras(args, ba, torch, stream, main):
+    ex = {}
+    # streaming-only workload: n = 1e10, d = 100, 1e12 edges, degree count of nodes < 1e5
+    g = W.STREAM_HUGE
+    counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+    ts = _time_events(lambda: ba.ba_degree_count(g.seed, g.n, g.d, NODE_LIMIT, counts, stream),
+                      stream, torch, 2)
+    ex["stream_huge_degree"] = {"workload": "n=1e10 d=100 seed=7, 1e12 edges, degree count of "
+                                            "nodes < 1e5 (section 3 experiment at 1/1000 scale)",
+                                "edges_per_s": g.m / min(ts), "seconds": min(ts),
+                                "degree_sum_first_1e5": int(counts.sum())}
+    # small workload, launch-dominated: median of repeated calls
+    s = W.PLAIN_SMALL
+    out_s = torch.empty((s.m, 2), dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        ba.ba_generate_edges(s.seed, s.n, s.d, 0, 0, s.m, out_s, stream)
+    ts = _time_events(lambda: ba.ba_generate_edges(s.seed, s.n, s.d, 0, 0, s.m, out_s, stream),
+                      stream, torch, 20)
+    ex["plain_small"] = {"workload": "n=1e6 d=4 seed=1, 4e6 edges (64 MB)",
+                         "edges_per_s": s.m / statistics.median(ts), "ms": 1e3 * statistics.median(ts)}
+    del out_s
+    # batched: first wave (<= 2^31 edges) of the 4096-graph table, one persistent launch
+    table = W.batch_table()
+    graphs, total = [], 0
+    for gg in table:
+        if total + gg.m > 2**31:
+            continue
+        graphs.append((gg.seed, gg.n, gg.d, gg.n0, 0, gg.m))
+        total += gg.m
+    plan = ba.ba_batch_plan_create(graphs)
+    try:
+        out_b = torch.empty((total, 2), dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            ba.ba_batch_plan_launch(plan, out_b, stream)
+        ts = _time_events(lambda: ba.ba_batch_plan_launch(plan, out_b, stream), stream, torch, 5)
+    finally:
+        ba.ba_batch_plan_destroy(plan)
+    plain_rate = 2**31 / (main["kernels_ms"]["generate"] / 1e3)
+    ex["batched"] = {"workload": f"{len(graphs)} graphs of the 4096-graph table (seed 1000+g, "
+                                 f"n log-uniform 1e3..1e7, d 1..32, half clique seeds), "
+                                 f"{total} edges in one persistent launch (CUDA graph replay)",
+                     "graphs": len(graphs), "edges": total,
+                     "edges_per_s": total / statistics.median(ts),
+                     "vs_plain": (total / statistics.median(ts)) / plain_rate}
+    del out_b
+    torch.cuda.empty_cache()
+    ex["serving"] = serving(args, ba, torch, plain_rate)
+    return ex
+
+
+def serving(args, ba, torch, plain_rate):
+    trace = W.serving_trace(rate=2000.0, duration=args.serve_seconds)
+    srv = ba.ba_server_create(memory_budget_bytes=96 << 30, chunk_edges=1 << 24, max_active=256)
+    lat = []
+    edges = 0
+    try:
+        done = []
+        lock = threading.Lock()
+
+        def submitter():
+            t0 = time.perf_counter()
+            for r in trace:
+                delay = r.t_arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                t = ba.ba_server_submit(srv, r.graph.seed, r.graph.n, r.graph.d, 0,
+                                        r.edge_begin, r.edge_end)
+                with lock:
+                    done.append((t, r.edge_end - r.edge_begin))
+
+        th = threading.Thread(target=submitter)
+        t_start = time.perf_counter()
+        th.start()
+        k = 0
+        while th.is_alive() or k < len(done):
+            with lock:
+                pending = done[k:]
+            if not pending:
+                time.sleep(0.0005)
+                continue
+            for t, length in pending:
+                ba.ba_server_wait(srv, t, 600_000)
+                _, l_ns = ba.ba_server_poll(srv, t)
+                lat.append(l_ns / 1e6)
+                edges += length
+                ba.ba_server_release(srv, t)
+                k += 1
+        th.join()
+        wall = time.perf_counter() - t_start
+        stats = ba.ba_server_stats_get(srv)
+        # saturation: the same requests all at once
+        t0 = time.perf_counter()
+        tickets = [ba.ba_server_submit(srv, r.graph.seed, r.graph.n, r.graph.d, 0, r.edge_begin,
+                                       r.edge_end) for r in trace[:4000]]
+        sat_edges = 0
+        for t, r in zip(tickets, trace[:4000]):
+            ba.ba_server_wait(srv, t, 600_000)
+            sat_edges += r.edge_end - r.edge_begin
+            ba.ba_server_release(srv, t)
+        sat_dt = time.perf_counter() - t0
+    finally:
+        ba.ba_server_destroy(srv)
+    lat.sort()
+    return {"workload": f"Poisson 2000 req/s for {args.serve_seconds:g} s ({len(trace)} requests; "
+                        "n log-uniform 1e4..1e9, d in {2,4,8,16,32}, 1e4..1e8 edges each)",
+            "p50_ms": lat[len(lat) // 2] if lat else None,
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+            "edges_per_s_offered_load": edges / wall, "requests": len(lat),
+            "ticks": stats["ticks"],
+            "saturation_edges_per_s": sat_edges / sat_dt,
+            "saturation_vs_plain": (sat_edges / sat_dt) / plain_rate}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

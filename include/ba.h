@@ -1,0 +1,271 @@
+/*
+ * ba.h -- C ABI of libba, GB300-native (sm_103a) Barabasi-Albert edge generation after
+ * Sanders & Schulz, "Scalable Generation of Scale-free Graphs" (arXiv:1602.07106).
+ *
+ * The graph (paper, sections 1, 2 and 4).  Nodes 0..n0-1 form the seed network, here the
+ * clique on n0 nodes with m0 = n0(n0-1)/2 edges listed (1,0),(2,0),(2,1),(3,0),... -- edge
+ * k = v(v-1)/2 + u is (v, u), u < v.  Every later node n0+j owns d edges, so there are
+ * m = m0 + (n-n0) d edges, numbered 0..m-1.  Edge i is the pair (E[2i], E[2i+1]) of the
+ * Batagelj-Brandes array: E[2i] is the owning node, n0 + floor((i-m0)/d), and E[2i+1] is
+ * E[x] for x = h(2i+1), uniform on 0..2i.  Fig. 1: start at r = 2i+1 and set r := h(r)
+ * until r is even (or, with a seed graph, r < 2m0, section 4); the target is then
+ * n0 + floor((r/2 - m0)/d) (or the seed clique's entry E[r]).
+ *
+ * The hash.  Section 2 asks for h(r) mapping a position r to a pseudo-random value in
+ * 0..r-1.  libba fixes
+ *     h(r) = floor( z * r / 2^64 ),   z = mix(seed XOR (r * 0x9E3779B97F4A7C15 mod 2^64)),
+ * mix = the SplitMix64 finaliser (Steele, Lea & Flood 2014):
+ *     z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB; z ^= z>>31.
+ * The graph is a pure function of (seed, n, d, n0): any split of the edge range, any
+ * launch shape and every entry point below give the same bits (section 2: the graph
+ * depends only on the hash, not on the number of processors).
+ *
+ * Conventions for every call:
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Device work is enqueued on it asynchronously; results are valid once the stream
+ *    has reached the call.  Pointers named *_dev / out / counts are device pointers owned
+ *    by the caller; libba neither frees nor keeps them, except where a call says so.
+ *  - Node IDs are written as int64 (all IDs are < 2^63), edges as (source, target)
+ *    pairs, source >= target, in edge-ID order.
+ *  - Argument rules: d >= 1, n >= 1, n0 <= n (else BA_ERR_INVALID_ARG); m <= 2^62 (else
+ *    BA_ERR_OVERFLOW); edge_begin <= edge_end <= m (else BA_ERR_RANGE); a non-empty
+ *    range needs a non-NULL, 16-byte aligned `out` (else BA_ERR_INVALID_ARG).  An empty
+ *    range returns BA_OK without touching the device.  A failing CUDA call returns
+ *    BA_ERR_CUDA; ba_last_error_message() then gives its text (per thread).
+ *  - Calls that take the same output pointer on different streams race; calls on
+ *    different streams with different outputs may overlap freely.
+ */
+#ifndef BA_H
+#define BA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ba_status {
+    BA_OK = 0,
+    BA_ERR_INVALID_ARG = 1,  /* malformed parameters or pointers */
+    BA_ERR_RANGE = 2,        /* edge range outside 0..m */
+    BA_ERR_OVERFLOW = 3,     /* m > 2^62, positions would not fit 64 bits */
+    BA_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    BA_ERR_NOMEM = 5,        /* device memory (or a server's budget) exhausted */
+    BA_ERR_TIMEOUT = 6,      /* a bounded wait ran out */
+    BA_ERR_BUSY = 7,         /* not admitted yet (server full); retry later */
+    BA_ERR_NOT_FOUND = 8     /* unknown ticket or key */
+} ba_status;
+
+/* Text for a status code; never NULL. */
+const char *ba_status_string(int status);
+
+/* Text of the last error raised on the calling thread (CUDA error string or a
+ * validation message); "" when none.  The pointer stays valid until the next libba call
+ * on this thread. */
+const char *ba_last_error_message(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int ba_version(void);
+
+/* m = n0(n0-1)/2 + (n-n0) d (section 4), or 0 when (n, d, n0) breaks the argument rules
+ * or m > 2^62. */
+uint64_t ba_num_edges(uint64_t n, uint32_t d, uint64_t n0);
+
+/*
+ * Fig. 1 (generateEdge) for every edge i in [edge_begin, edge_end) of the graph
+ * (seed, n, d, n0).  out_dev: 2*(edge_end-edge_begin) int64, 16-byte aligned; edge i is
+ * written to out_dev[2(i-edge_begin)] (source) and out_dev[2(i-edge_begin)+1] (target).
+ * Runs the persistent warp-refill kernel (tiles handed out dynamically, section 2's
+ * batches of edge IDs) with the launch shape from the tuner cache.
+ */
+ba_status ba_generate_edges(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                            uint64_t edge_begin, uint64_t edge_end,
+                            int64_t *out_dev, void *stream);
+
+/*
+ * Same result as ba_generate_edges, written to HOST memory: host_out holds
+ * 2*(edge_end-edge_begin) int64 (pinned memory gives full copy speed; pageable memory
+ * works but is slower).  The range is generated in chunks into device staging buffers
+ * allocated from the stream's memory pool and copied out while the next chunk is
+ * generated.  Returns after the whole result is in host_out (synchronises `stream`).
+ */
+ba_status ba_generate_edges_host(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                 uint64_t edge_begin, uint64_t edge_end,
+                                 int64_t *host_out, void *stream);
+
+/*
+ * Section 3's streaming analysis: the degree (number of end points, a self-loop counting
+ * twice) of nodes 0..node_limit-1 over ALL m edges of the graph (seed, n, d) with an
+ * empty seed graph (n0 = 0), without storing any edge.  counts_dev: node_limit uint64,
+ * 8-byte aligned, overwritten.  node_limit may exceed n (the extra entries are 0);
+ * node_limit = 0 is a no-op.
+ */
+ba_status ba_degree_count(uint64_t seed, uint64_t n, uint32_t d, uint64_t node_limit,
+                          uint64_t *counts_dev, void *stream);
+
+/*
+ * As ba_degree_count, for the edges [edge_begin, edge_end) of the graph (seed, n, d, n0).
+ * accumulate = 0 overwrites counts_dev, accumulate != 0 adds to it, so that the counts
+ * of any split of 0..m into ranges sum to the counts of the whole graph.
+ */
+ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                uint64_t edge_begin, uint64_t edge_end,
+                                uint64_t node_limit, uint64_t *counts_dev,
+                                int accumulate, void *stream);
+
+/* ------------------------------------------------------------------ launch shapes -- */
+
+/* Launch shape of the generate and degree kernels.  Zero fields mean "library default".
+ *  block        threads per CTA (multiple of 32, <= 1024)
+ *  ctas_per_sm  resident CTAs per SM of the persistent grid
+ *  tile         edges per warp tile (power of two, 64..4096)
+ *  refill       0 = one thread per edge, no refill (the simple kernel);
+ *               1 = warp refill every hash step (ballot/popc compaction)
+ *  hist_bins    degree kernel: shared-memory histogram bins per CTA */
+typedef struct ba_tuning {
+    int32_t block;
+    int32_t ctas_per_sm;
+    int32_t tile;
+    int32_t refill;
+    int32_t hist_bins;
+    int32_t reserved[3];
+} ba_tuning;
+
+/* Kernel families the tuner keys on. */
+enum { BA_KIND_GENERATE = 0, BA_KIND_DEGREE = 1, BA_KIND_BATCH = 2 };
+
+/* Overrides the launch shape used for `kind` (NULL restores the tuned/default shape).
+ * Output never depends on the shape (tests check this). */
+ba_status ba_set_tuning(int32_t kind, const ba_tuning *tune);
+
+/* The shape a call of `kind` would use now for an edge range ending at edge_end. */
+ba_status ba_get_tuning(int32_t kind, uint64_t edge_end, ba_tuning *out);
+
+/*
+ * Autotuner: times candidate shapes (block size, CTAs/SM, tile, refill, histogram
+ * bins) for `kind` on the sample graph (seed, n, d, n0) range [0, edge_end) -- for
+ * BA_KIND_GENERATE it needs scratch_dev of 2*edge_end int64 -- keeps the fastest in the
+ * in-process cache (keyed by kind and 32/64-bit position path) and writes it to
+ * out (may be NULL).  Synchronises `stream`.
+ */
+ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                  uint64_t edge_end, int64_t *scratch_dev, void *stream, ba_tuning *out);
+
+/* Save / load the tuner cache as JSON text (path NULL = $BA_TUNE_CACHE).  The cache is
+ * loaded automatically from $BA_TUNE_CACHE at the first call when that variable is set. */
+ba_status ba_tune_save(const char *path);
+ba_status ba_tune_load(const char *path);
+
+/* ---------------------------------------------------------- batched generation -- */
+
+/* One graph of a batch: its parameters and the edge range [edge_begin, edge_end) to emit. */
+typedef struct ba_graph_desc {
+    uint64_t seed;
+    uint64_t n;
+    uint64_t n0;
+    uint64_t edge_begin;
+    uint64_t edge_end;
+    uint32_t d;
+    uint32_t reserved;
+} ba_graph_desc;
+
+typedef struct ba_batch_plan ba_batch_plan;
+
+/*
+ * Plans one persistent launch over G graphs (section 2's batches of edge IDs, across
+ * graphs).  descs (host, G entries) are validated and copied; out_offsets (host, G+1
+ * int64, may be NULL = packed) gives where graph g's edges go: graph g's edge
+ * edge_begin+k is written to out[2*(out_offsets[g]+k)], and out_offsets must be
+ * non-decreasing with out_offsets[g+1]-out_offsets[g] >= edge_end-edge_begin.  The plan
+ * owns a device copy of the descriptor table and the per-graph tile prefix, and a CUDA
+ * graph of the launch, instantiated on the first ba_batch_plan_launch.
+ * tune may be NULL (tuned/default shape for BA_KIND_BATCH).
+ */
+ba_status ba_batch_plan_create(const ba_graph_desc *descs, int32_t G,
+                               const int64_t *out_offsets, const ba_tuning *tune,
+                               ba_batch_plan **plan);
+
+/* Total output edges of the plan (= out_offsets[G], or the packed sum). */
+uint64_t ba_batch_plan_total_edges(const ba_batch_plan *plan);
+
+/* Copies the plan's G+1 output offsets (in edges) to host memory. */
+ba_status ba_batch_plan_offsets(const ba_batch_plan *plan, int64_t *host_offsets);
+
+/* Replays the plan's CUDA graph on `stream`, writing into out_dev (16-byte aligned,
+ * 2*total_edges int64).  The first call (and any call with another stream or out_dev)
+ * captures or updates the graph. */
+ba_status ba_batch_plan_launch(ba_batch_plan *plan, int64_t *out_dev, void *stream);
+
+/* Waits for nothing; frees the plan's device tables and graph after the device work
+ * already enqueued with it. */
+ba_status ba_batch_plan_destroy(ba_batch_plan *plan);
+
+/* One-shot form: plan, launch once, destroy.  offsets_host as in ba_batch_plan_create. */
+ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
+                            const int64_t *offsets_host, int64_t *out_dev,
+                            const ba_tuning *tune, void *stream);
+
+/* ------------------------------------------------- serving (continuous batching) -- */
+
+typedef struct ba_server ba_server;
+
+typedef struct ba_server_config {
+    uint64_t memory_budget_bytes;  /* device bytes for output buffers (0 = 50% of free) */
+    uint64_t chunk_edges;          /* edges per request per tick (0 = 1<<24) */
+    int32_t max_active;            /* requests on the device at once (0 = 256) */
+    int32_t max_inflight_ticks;    /* ticks enqueued ahead of the GPU (0 = 2) */
+    int32_t device;                /* CUDA device ordinal (-1 = current) */
+    int32_t reserved;
+} ba_server_config;
+
+typedef struct ba_server_stats {
+    uint64_t submitted, admitted, completed, released, rejected_busy;
+    uint64_t ticks, edges_done, bytes_in_use, queue_depth, active;
+} ba_server_stats;
+
+/* Request states reported by ba_server_poll. */
+enum { BA_REQ_QUEUED = 0, BA_REQ_RUNNING = 1, BA_REQ_DONE = 2, BA_REQ_FAILED = 3 };
+
+/*
+ * Starts a server: a scheduler thread that admits queued edge-range requests while the
+ * memory budget and max_active allow, and on every tick packs the next chunk of every
+ * running request into one batched launch (ba_batch plan machinery), so that requests
+ * arriving while others run join the next tick.  Output buffers live on the device until
+ * ba_server_release.
+ */
+ba_status ba_server_create(const ba_server_config *cfg, ba_server **server);
+
+/* Queues a request (n0 must be 0 or a clique seed graph like every other call); returns
+ * its ticket.  BA_ERR_NOMEM if the request alone exceeds the budget. */
+ba_status ba_server_submit(ba_server *server, const ba_graph_desc *req, uint64_t *ticket);
+
+/* State (BA_REQ_*) of a ticket; for DONE/FAILED also the submit-to-completion latency in
+ * nanoseconds (latency_ns may be NULL). */
+ba_status ba_server_poll(ba_server *server, uint64_t ticket, int32_t *state,
+                         uint64_t *latency_ns);
+
+/* Blocks until the ticket is DONE or FAILED or timeout_ms passes (BA_ERR_TIMEOUT). */
+ba_status ba_server_wait(ba_server *server, uint64_t ticket, int64_t timeout_ms);
+
+/* Device pointer and edge count of a DONE request (valid until ba_server_release). */
+ba_status ba_server_result(ba_server *server, uint64_t ticket, const int64_t **out_dev,
+                           uint64_t *n_edges);
+
+/* Copies a DONE request's 2*n_edges int64 into dst (device or host memory, 16-byte
+ * aligned not required) on `stream`; the copy is ordered after the request's work. */
+ba_status ba_server_copy_result(ba_server *server, uint64_t ticket, int64_t *dst, void *stream);
+
+/* Frees a finished request's buffer, returning its bytes to the budget. */
+ba_status ba_server_release(ba_server *server, uint64_t ticket);
+
+ba_status ba_server_stats_get(ba_server *server, ba_server_stats *stats);
+
+/* Stops the scheduler (queued requests are dropped, running ones finish), frees all
+ * buffers. */
+ba_status ba_server_destroy(ba_server *server);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BA_H */

@@ -1,0 +1,282 @@
+// ba_api.cu -- the C ABI of libba (include/ba.h): argument checks, per-call scratch and
+// the launches of the plain entry points.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+namespace {
+thread_local std::string g_last_error;
+
+// Per-call scratch from the stream-ordered allocator: freed on the same stream once the
+// work enqueued before the free has run, so concurrent calls never share it.
+struct StreamScratch {
+  void *ptr = nullptr;
+  cudaStream_t stream = nullptr;
+  ba_status alloc(size_t bytes, cudaStream_t s) {
+    stream = s;
+    cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+    if (e != cudaSuccess) {
+      ptr = nullptr;
+      return e == cudaErrorMemoryAllocation ? (set_error("cudaMallocAsync: out of memory"), BA_ERR_NOMEM)
+                                            : cuda_fail(e, "cudaMallocAsync");
+    }
+    return BA_OK;
+  }
+  void release() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+  }
+  ~StreamScratch() { release(); }
+};
+
+std::mutex g_sm_mutex;
+std::vector<int> g_sm_counts;
+}  // namespace
+
+void set_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+ba_status cuda_fail(cudaError_t e, const char *where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return BA_ERR_CUDA;
+}
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(g_sm_mutex);
+  if (dev >= static_cast<int>(g_sm_counts.size())) g_sm_counts.resize(dev + 1, 0);
+  if (g_sm_counts[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_counts[dev] = std::max(n, 1);
+  }
+  return g_sm_counts[dev];
+}
+
+ba_status validate_graph(uint64_t n, uint32_t d, uint64_t n0, uint64_t *m_out) {
+  if (n == 0 || d == 0 || n0 > n) {
+    set_error("graph parameters need n >= 1, d >= 1 and n0 <= n");
+    return BA_ERR_INVALID_ARG;
+  }
+  const unsigned __int128 m0 = n0 > 0 ? (static_cast<unsigned __int128>(n0) * (n0 - 1)) / 2 : 0;
+  const unsigned __int128 m = m0 + static_cast<unsigned __int128>(n - n0) * d;
+  if (m > (static_cast<unsigned __int128>(1) << 62)) {
+    set_error("m exceeds 2^62 edges: positions 2m would not fit 64 bits");
+    return BA_ERR_OVERFLOW;
+  }
+  *m_out = static_cast<uint64_t>(m);
+  return BA_OK;
+}
+
+GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint64_t begin,
+                        uint64_t end) {
+  GraphDev g{};
+  g.seed = seed;
+  g.n = n;
+  g.n0 = n0;
+  g.m0 = n0 > 0 ? n0 * (n0 - 1) / 2 : 0;
+  g.two_m0 = 2 * g.m0;
+  g.begin = begin;
+  g.end = end;
+  g.out_edge = 0;
+  g.tile0 = 0;
+  g.d = d;
+  const uint32_t l = d == 1 ? 0 : 32 - __builtin_clz(d - 1);  // ceil(log2 d)
+  const unsigned __int128 one = 1;
+  g.div.l = l;
+  g.div.m64 = static_cast<uint64_t>(((one << (62 + l)) + d - 1) / d);
+  g.div.p32 = 31 + l;
+  g.div.m32 = static_cast<uint32_t>(((one << (31 + l)) + d - 1) / d);
+  return g;
+}
+
+}  // namespace ba
+
+using namespace ba;
+
+namespace {
+
+ba_status check_range(uint64_t n, uint32_t d, uint64_t n0, uint64_t begin, uint64_t end,
+                      uint64_t *m) {
+  ba_status st = validate_graph(n, d, n0, m);
+  if (st != BA_OK) return st;
+  if (begin > end || end > *m) {
+    set_error("edge range must satisfy edge_begin <= edge_end <= m");
+    return BA_ERR_RANGE;
+  }
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ba_status_string(int status) {
+  switch (status) {
+    case BA_OK: return "ok";
+    case BA_ERR_INVALID_ARG: return "invalid argument";
+    case BA_ERR_RANGE: return "edge range outside 0..m";
+    case BA_ERR_OVERFLOW: return "graph too large (m > 2^62)";
+    case BA_ERR_CUDA: return "CUDA error";
+    case BA_ERR_NOMEM: return "out of memory";
+    case BA_ERR_TIMEOUT: return "timed out";
+    case BA_ERR_BUSY: return "busy";
+    case BA_ERR_NOT_FOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char *ba_last_error_message(void) { return g_last_error.c_str(); }
+
+int ba_version(void) { return 10000; }
+
+uint64_t ba_num_edges(uint64_t n, uint32_t d, uint64_t n0) {
+  uint64_t m = 0;
+  std::string saved = g_last_error;
+  ba_status st = validate_graph(n, d, n0, &m);
+  g_last_error = saved;
+  return st == BA_OK ? m : 0;
+}
+
+ba_status ba_generate_edges(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                            uint64_t edge_begin, uint64_t edge_end, int64_t *out_dev,
+                            void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  if (edge_begin == edge_end) return BA_OK;
+  if (out_dev == nullptr || (reinterpret_cast<uintptr_t>(out_dev) & 15) != 0) {
+    set_error("out must be a non-NULL, 16-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  const Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  StreamScratch scratch;
+  if (shape.refill != 0) {
+    st = scratch.alloc(sizeof(unsigned long long), s);
+    if (st != BA_OK) return st;
+  }
+  return launch_generate(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr), s);
+}
+
+ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                uint64_t edge_begin, uint64_t edge_end, uint64_t node_limit,
+                                uint64_t *counts_dev, int accumulate, void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  if (node_limit == 0) return BA_OK;
+  if (counts_dev == nullptr || (reinterpret_cast<uintptr_t>(counts_dev) & 7) != 0) {
+    set_error("counts must be a non-NULL, 8-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (node_limit > (1ull << 40)) {
+    set_error("node_limit above 2^40 counters");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  const Shape shape = shape_for(BA_KIND_DEGREE, edge_end <= (1ull << 31));
+  StreamScratch scratch;
+  st = scratch.alloc(sizeof(unsigned long long), s);
+  if (st != BA_OK) return st;
+  return launch_degree(g, node_limit, counts_dev, accumulate, shape,
+                       static_cast<unsigned long long *>(scratch.ptr), s);
+}
+
+ba_status ba_degree_count(uint64_t seed, uint64_t n, uint32_t d, uint64_t node_limit,
+                          uint64_t *counts_dev, void *stream) {
+  uint64_t m = 0;
+  ba_status st = validate_graph(n, d, 0, &m);
+  if (st != BA_OK) return st;
+  return ba_degree_count_range(seed, n, d, 0, 0, m, node_limit, counts_dev, 0, stream);
+}
+
+ba_status ba_generate_edges_host(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                 uint64_t edge_begin, uint64_t edge_end, int64_t *host_out,
+                                 void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  if (edge_begin == edge_end) return BA_OK;
+  if (host_out == nullptr) {
+    set_error("host_out must be non-NULL");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t total = edge_end - edge_begin;
+  const uint64_t chunk = std::min<uint64_t>(total, 1ull << 25);  // 512 MB of pairs
+  const int nbuf = total > chunk ? 2 : 1;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t produced[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+  StreamScratch bufs[2];
+  auto cleanup = [&]() {
+    for (int b = 0; b < 2; ++b) {
+      if (produced[b]) cudaEventDestroy(produced[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+  for (int b = 0; b < nbuf; ++b) {
+    if ((e = cudaEventCreateWithFlags(&produced[b], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
+    st = bufs[b].alloc(chunk * 2 * sizeof(int64_t), s);
+    if (st != BA_OK) {
+      cleanup();
+      return st;
+    }
+  }
+  const Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  StreamScratch counter;
+  if ((st = counter.alloc(sizeof(unsigned long long), s)) != BA_OK) {
+    cleanup();
+    return st;
+  }
+  uint64_t k = 0;
+  for (uint64_t a = edge_begin; a < edge_end; a += chunk, ++k) {
+    const int b = static_cast<int>(k % nbuf);
+    const uint64_t end = std::min(edge_end, a + chunk);
+    if (k >= static_cast<uint64_t>(nbuf)) cudaStreamWaitEvent(s, copied[b], 0);  // buffer free
+    const GraphDev g = make_graph_dev(seed, n, d, n0, a, end);
+    st = launch_generate(g, static_cast<int64_t *>(bufs[b].ptr), shape,
+                         static_cast<unsigned long long *>(counter.ptr), s);
+    if (st != BA_OK) break;
+    cudaEventRecord(produced[b], s);
+    cudaStreamWaitEvent(copy_stream, produced[b], 0);
+    e = cudaMemcpyAsync(host_out + 2 * (a - edge_begin), bufs[b].ptr, (end - a) * 2 * sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, copy_stream);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "cudaMemcpyAsync");
+      break;
+    }
+    cudaEventRecord(copied[b], copy_stream);
+  }
+  e = cudaStreamSynchronize(copy_stream);
+  if (st == BA_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+  // buffers are freed on `s` after the copies finished
+  for (int b = 0; b < nbuf; ++b) cudaStreamWaitEvent(s, copied[b], 0);
+  bufs[0].release();
+  bufs[1].release();
+  e = cudaStreamSynchronize(s);
+  if (st == BA_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+  cleanup();
+  return st;
+}
+
+}  // extern "C"

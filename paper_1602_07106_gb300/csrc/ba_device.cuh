@@ -1,0 +1,159 @@
+// ba_device.cuh -- device-side arithmetic of generateEdge (paper Fig. 1, section 4).
+//
+// Everything here is integer arithmetic on the CUDA cores: no tensor cores, since the
+// work is hashing, not a contraction.  Two position paths compute identical values:
+//   * R32: every position r < 2^32 (ranges with edge_end <= 2^31).  r*G and the final
+//     multiply-high need two 32x32->64 IMADs each instead of a full 64x64 product;
+//     the paper's observation that 32-bit arithmetic is much cheaper (section 3),
+//     applied to positions only -- node IDs are still written as int64.
+//   * R64: any position r < 2^63.
+#pragma once
+#include <cstdint>
+
+namespace ba {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment (golden ratio)
+constexpr uint64_t kMixA = 0xBF58476D1CE4E5B9ull;   // SplitMix64 finaliser multipliers
+constexpr uint64_t kMixB = 0x94D049BB133111EBull;
+
+// SplitMix64 finaliser (Steele, Lea & Flood 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * kMixA;
+  z = (z ^ (z >> 27)) * kMixB;
+  return z ^ (z >> 31);
+}
+
+// h(r) in 0..r-1 for r < 2^32.  floor(z*r/2^64) = floor((z_hi*r + floor(z_lo*r/2^32))/2^32),
+// and z_hi*r + floor(z_lo*r/2^32) < 2^64, so one IMAD.HI and one wide IMAD suffice.
+__device__ __forceinline__ uint32_t hash_r32(uint64_t seed, uint32_t r) {
+  const uint64_t z = mix64(seed ^ (static_cast<uint64_t>(r) * kGamma));
+  const uint32_t zlo = static_cast<uint32_t>(z);
+  const uint32_t zhi = static_cast<uint32_t>(z >> 32);
+  const uint32_t t = __umulhi(zlo, r);
+  return static_cast<uint32_t>((static_cast<uint64_t>(zhi) * r + t) >> 32);
+}
+
+// h(r) in 0..r-1 for any r.
+__device__ __forceinline__ uint64_t hash_r64(uint64_t seed, uint64_t r) {
+  return __umul64hi(mix64(seed ^ (r * kGamma)), r);
+}
+
+template <class RT>
+__device__ __forceinline__ RT hash_pos(uint64_t seed, RT r);
+template <>
+__device__ __forceinline__ uint32_t hash_pos<uint32_t>(uint64_t seed, uint32_t r) {
+  return hash_r32(seed, r);
+}
+template <>
+__device__ __forceinline__ uint64_t hash_pos<uint64_t>(uint64_t seed, uint64_t r) {
+  return hash_r64(seed, r);
+}
+
+// Division by the constant d (Granlund & Montgomery 1994, multiply-high by a rounded-up
+// reciprocal).  With l = ceil(log2 d):
+//   64-bit numerators x < 2^62:  M = ceil(2^(62+l)/d) < 2^64,  x/d = umulhi(4x, M) >> l
+//   31-bit numerators x < 2^31:  M = ceil(2^(31+l)/d) < 2^32,  x/d = (x*M) >> (31+l)
+// Exact because x*(M*d - 2^p) < 2^p in both cases.
+struct FastDiv {
+  uint64_t m64;
+  uint32_t l;
+  uint32_t m32;
+  uint32_t p32;
+  uint32_t pad;
+};
+
+__device__ __forceinline__ uint64_t div64(uint64_t x, const FastDiv &f) {
+  return __umul64hi(x << 2, f.m64) >> f.l;
+}
+__device__ __forceinline__ uint32_t div32(uint32_t x, const FastDiv &f) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(x) * f.m32) >> f.p32);
+}
+
+// Seed clique (section 4): position p < 2 m0 belongs to seed edge k = p/2 = v(v-1)/2 + u,
+// E[2k] = v, E[2k+1] = u.  v comes from the quadratic formula, corrected to the exact
+// integer (the estimate is off by at most one).  Rare on the hot path.
+__device__ __forceinline__ uint64_t clique_position(uint64_t p) {
+  const uint64_t k = p >> 1;
+  uint64_t v = static_cast<uint64_t>((1.0 + sqrt(8.0 * static_cast<double>(k) + 1.0)) * 0.5);
+  while (v > 1 && v * (v - 1) / 2 > k) --v;
+  while (v * (v + 1) / 2 <= k) ++v;
+  return (p & 1) ? k - v * (v - 1) / 2 : v;
+}
+
+// Per-graph constants, computed on the host (make_graph_dev in ba_api.cu).
+struct GraphDev {
+  uint64_t seed;
+  uint64_t n;         // nodes
+  uint64_t n0;        // first non-seed node
+  uint64_t m0;        // seed edges
+  uint64_t two_m0;    // positions below this are seed positions
+  uint64_t begin;     // edge range [begin, end) to emit
+  uint64_t end;
+  uint64_t out_edge;  // output slot (in edges) of edge `begin`
+  uint64_t tile0;     // first global tile of this graph (batched launches)
+  FastDiv div;        // division by d
+  uint32_t d;
+  uint32_t pad;
+};
+
+// E[2i]: the owner of edge i (clique edge for i < m0).
+template <class RT, bool HasSeed>
+__device__ __forceinline__ uint64_t source_of(uint64_t i, const GraphDev &g) {
+  if (HasSeed && i < g.m0) return clique_position(2 * i);
+  if constexpr (sizeof(RT) == 4) {
+    return g.n0 + div32(static_cast<uint32_t>(i - g.m0), g.div);
+  } else {
+    return g.n0 + div64(i - g.m0, g.div);
+  }
+}
+
+// E[r] for the position r where the chain of Fig. 1 stopped (even, or a seed position).
+template <class RT, bool HasSeed>
+__device__ __forceinline__ uint64_t target_of(RT r, const GraphDev &g) {
+  if (HasSeed && r < g.two_m0) return clique_position(r);
+  if constexpr (sizeof(RT) == 4) {
+    return g.n0 + div32((r >> 1) - static_cast<uint32_t>(g.m0), g.div);
+  } else {
+    return g.n0 + div64((r >> 1) - g.m0, g.div);
+  }
+}
+
+// 2 m0 as a position of type RT.  On the 32-bit path a seed larger than every position
+// in range saturates: every chain then stops in the seed, as it must.
+template <class RT>
+__device__ __forceinline__ RT seed_limit(uint64_t two_m0) {
+  if constexpr (sizeof(RT) == 4) return two_m0 > 0xffffffffull ? 0xffffffffu : static_cast<RT>(two_m0);
+  else return two_m0;
+}
+
+// Does the chain stop at position r?  (Fig. 1: r even; section 4: r inside the seed.)
+template <class RT, bool HasSeed>
+__device__ __forceinline__ bool chain_stops(RT r, RT two_m0) {
+  return ((r & 1) == 0) || (HasSeed && r < two_m0);
+}
+
+// generateEdge(i), Fig. 1, one edge at a time.
+template <class RT, bool HasSeed>
+__device__ __forceinline__ void generate_edge(uint64_t i, const GraphDev &g, uint64_t &u,
+                                              uint64_t &v) {
+  if (HasSeed && i < g.m0) {
+    u = clique_position(2 * i);
+    v = clique_position(2 * i + 1);
+    return;
+  }
+  RT r = static_cast<RT>(2 * i + 1);
+  const RT two_m0 = seed_limit<RT>(g.two_m0);
+  do {
+    r = hash_pos<RT>(g.seed, r);
+  } while (!chain_stops<RT, HasSeed>(r, two_m0));
+  u = source_of<RT, HasSeed>(i, g);
+  v = target_of<RT, HasSeed>(r, g);
+}
+
+// 16-byte streaming store of one (source, target) pair.
+__device__ __forceinline__ void store_edge(int64_t *out, uint64_t k, uint64_t u, uint64_t v) {
+  __stcs(reinterpret_cast<longlong2 *>(out) + k,
+         make_longlong2(static_cast<long long>(u), static_cast<long long>(v)));
+}
+
+}  // namespace ba

@@ -1,0 +1,64 @@
+// ba_internal.h -- host-side interfaces shared by libba's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/ba.h"
+#include "ba_device.cuh"
+
+namespace ba {
+
+// Persistent-scheduler parameters of one launch.
+struct SchedParams {
+  uint64_t num_tiles;            // tiles of 2^tile_shift edges over the whole launch
+  unsigned long long *counter;   // zeroed before the launch; tiles past the first wave
+  uint32_t tile_shift;
+  uint32_t total_warps;          // warps in the grid (first tile of warp w is w)
+};
+
+// Graph table of a batched launch (device pointers).
+struct BatchTable {
+  const GraphDev *graphs;        // G entries
+  const uint64_t *tile_prefix;   // G+1 entries: graph g owns tiles [tile_prefix[g], [g+1])
+  int32_t G;
+};
+
+struct Shape {
+  int block = 0;
+  int ctas_per_sm = 0;
+  int tile = 0;
+  int refill = 1;
+  int hist_bins = 0;
+};
+
+// ---- host helpers (ba_api.cu)
+void set_error(const char *msg);
+ba_status cuda_fail(cudaError_t e, const char *where);
+GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint64_t begin,
+                        uint64_t end);
+ba_status validate_graph(uint64_t n, uint32_t d, uint64_t n0, uint64_t *m_out);
+int sm_count();
+
+// ---- tuner cache (ba_tune.cu)
+Shape shape_for(int kind, bool r32);
+ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out);  // validates
+void shape_store(int kind, bool r32, const Shape &s);
+
+// ---- kernel launchers (ba_kernels.cu).  All enqueue on `stream` and return BA_OK or
+// BA_ERR_CUDA.  `counter` must point to >= 8 bytes of device memory; it is zeroed here.
+ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
+                          unsigned long long *counter, cudaStream_t stream);
+ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                        int accumulate, const Shape &s, unsigned long long *counter,
+                        cudaStream_t stream);
+ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,
+                       int64_t *out, const Shape &s, unsigned long long *counter,
+                       cudaStream_t stream);
+
+// Number of CUDA kernels the last launch_* call on this thread enqueued (for the
+// benchmark's launch count).
+int last_kernel_count();
+
+}  // namespace ba

@@ -1,0 +1,577 @@
+// ba_kernels.cu -- the sm_103a kernels of libba and their launchers.
+//
+// Generate (paper Fig. 1 over a range of edge IDs):
+//   k_generate_simple  one thread per edge, grid-stride; the parity baseline.
+//   k_generate_refill  persistent warps.  Each warp takes tiles of T edge IDs from a
+//                      global counter (section 2's dynamic load balancing by batches of
+//                      edge IDs).  Every step each busy lane applies one hash; lanes whose
+//                      chain stopped park the final position r in a shared-memory slot
+//                      of the tile and take the next edge ID of the tile by ballot/popc
+//                      compaction, so the geometric chain lengths do not leave lanes
+//                      idle.  A warp keeps two tile slots: it hands out edge IDs of the
+//                      newer tile while the older tile's last chains finish.  A finished
+//                      tile is written out by the whole warp: consecutive lanes store
+//                      consecutive 16-byte (source, target) pairs.
+// Degree count (section 3's streaming analysis, no edge stored):
+//   k_degree_init      sources and seed-clique end points in closed form.
+//   k_degree_simple    one thread per edge, global atomics.
+//   k_degree_refill    the refill scheduler of k_generate_refill; targets below the
+//                      shared-memory limit go to a per-CTA histogram with warp-aggregated
+//                      atomics (__match_any_sync), the rest to global 64-bit atomics.
+#include <algorithm>
+
+#include "ba_internal.h"
+
+namespace ba {
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+thread_local int g_kernel_count = 0;
+
+// ------------------------------------------------------------------ simple kernels --
+
+template <class RT, bool HasSeed>
+__global__ void k_generate_simple(const GraphDev g, int64_t *__restrict__ out) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = g.begin + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+       i < g.end; i += stride) {
+    uint64_t u, v;
+    generate_edge<RT, HasSeed>(i, g, u, v);
+    store_edge(out, g.out_edge + (i - g.begin), u, v);
+  }
+}
+
+// ------------------------------------------------------------ warp tile scheduling --
+
+// Takes the warp's next tile index: the first one is the warp's own index, later ones
+// come from the global counter.  Warp-collective.
+__device__ __forceinline__ uint64_t next_tile(const SchedParams &sp, bool &first,
+                                              uint64_t gwarp) {
+  if (first) {
+    first = false;
+    return gwarp;
+  }
+  unsigned long long t = 0;
+  if ((threadIdx.x & 31) == 0) t = atomicAdd(sp.counter, 1ull);
+  return __shfl_sync(kFull, t, 0) + sp.total_warps;
+}
+
+// Graph that owns global tile t of a batched launch (binary search in the tile prefix).
+__device__ __forceinline__ int graph_of_tile(const BatchTable &tab, uint64_t t) {
+  int lo = 0, hi = tab.G;  // tile_prefix[lo] <= t < tile_prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tab.tile_prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Warp-collective copy of one GraphDev into shared memory.
+__device__ __forceinline__ void copy_graph(GraphDev *dst, const GraphDev *src) {
+  constexpr int kWords = sizeof(GraphDev) / 8;
+  static_assert(sizeof(GraphDev) % 8 == 0, "GraphDev must be a whole number of words");
+  const int lane = threadIdx.x & 31;
+  if (lane < kWords)
+    reinterpret_cast<uint64_t *>(dst)[lane] = reinterpret_cast<const uint64_t *>(src)[lane];
+  __syncwarp();
+}
+
+// Writes the finished tile [base, base+len) of one slot: lane j of the warp handles
+// edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes.
+template <class RT, bool HasSeed>
+__device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint32_t len,
+                                           const GraphDev &g, int64_t *__restrict__ out) {
+  __syncwarp();
+  const uint64_t out0 = g.out_edge + (base - g.begin);
+  for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+    const uint64_t i = base + j;
+    uint64_t u, v;
+    if (HasSeed && i < g.m0) {
+      u = clique_position(2 * i);
+      v = clique_position(2 * i + 1);
+    } else {
+      u = source_of<RT, HasSeed>(i, g);
+      v = target_of<RT, HasSeed>(stage[j], g);
+    }
+    store_edge(out, out0 + j, u, v);
+  }
+  __syncwarp();
+}
+
+// ----------------------------------------------------------- refill generate kernel --
+
+template <class RT, bool HasSeed, bool Batched>
+__global__ void __launch_bounds__(1024)
+k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
+                  int64_t *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t shift = sp.tile_shift;
+  const uint32_t T = 1u << shift;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  RT *stage = reinterpret_cast<RT *>(smem_raw) + static_cast<size_t>(wib) * 2 * T;
+  GraphDev *sg = nullptr;
+  if constexpr (Batched)
+    sg = reinterpret_cast<GraphDev *>(smem_raw + static_cast<size_t>(warps) * 2 * T * sizeof(RT)) +
+         2 * wib;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + wib;
+  bool first = true;
+
+  // Loads tile t into slot `slot`; false when the launch has no tile t.
+  auto fetch = [&](int slot, uint64_t &base, uint32_t &len) -> bool {
+    const uint64_t t = next_tile(sp, first, gwarp);
+    if (t >= sp.num_tiles) return false;
+    if constexpr (Batched) {
+      const int gi = graph_of_tile(tab, t);
+      copy_graph(sg + slot, tab.graphs + gi);
+      base = sg[slot].begin + ((t - sg[slot].tile0) << shift);
+      len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), sg[slot].end - base));
+    } else {
+      base = g0.begin + (t << shift);
+      len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g0.end - base));
+    }
+    return true;
+  };
+  auto flush = [&](int slot, uint64_t base, uint32_t len) {
+    if constexpr (Batched)
+      flush_tile<RT, HasSeed>(stage + (slot << shift), base, len, sg[slot], out);
+    else
+      flush_tile<RT, HasSeed>(stage + (slot << shift), base, len, g0, out);
+  };
+
+  // Warp-uniform slot state: `cur` is the tile being handed out, `oth` the older one.
+  int cur = 0, oth = 1;
+  uint64_t cur_base = 0, oth_base = 0;
+  uint32_t cur_len = 0, oth_len = 0, hoff = 0;
+  bool oth_live = false, tiles_left = true;
+  if (!fetch(cur, cur_base, cur_len)) return;
+
+  // Lane state.
+  bool busy = false;
+  RT r = 0;
+  uint32_t sidx = 0;
+  uint64_t lseed = g0.seed;
+  RT l2m0 = seed_limit<RT>(g0.two_m0);
+
+  for (;;) {
+    if (busy) {
+      r = hash_pos<RT>(lseed, r);
+      if (chain_stops<RT, HasSeed>(r, l2m0)) {
+        stage[sidx] = r;
+        busy = false;
+      }
+    }
+    const uint32_t fm = __ballot_sync(kFull, !busy);
+    if (fm == 0) continue;
+    const uint32_t nfree = __popc(fm);
+    const uint32_t rank = __popc(fm & lt);
+    uint32_t taken = 0;
+    while (taken < nfree) {
+      const uint32_t avail = cur_len - hoff;
+      if (avail > 0) {
+        const uint32_t k = min(avail, nfree - taken);
+        if (!busy && rank - taken < k) {
+          const uint32_t o = hoff + (rank - taken);
+          const uint64_t i = cur_base + o;
+          sidx = (static_cast<uint32_t>(cur) << shift) + o;
+          r = static_cast<RT>(2 * i + 1);
+          if constexpr (Batched) {
+            lseed = sg[cur].seed;
+            l2m0 = seed_limit<RT>(sg[cur].two_m0);
+          }
+          busy = true;
+        }
+        hoff += k;
+        taken += k;
+        continue;
+      }
+      if (!tiles_left) break;
+      if (oth_live) {
+        // The older slot is reused only after its last chain has stopped.
+        if (__any_sync(kFull, busy && (sidx >> shift) == static_cast<uint32_t>(oth))) break;
+        flush(oth, oth_base, oth_len);
+        oth_live = false;
+      }
+      uint64_t nb;
+      uint32_t nl;
+      if (!fetch(oth, nb, nl)) {
+        tiles_left = false;
+        break;
+      }
+      oth_base = cur_base;
+      oth_len = cur_len;
+      oth_live = true;
+      const int tmp = cur;
+      cur = oth;
+      oth = tmp;
+      cur_base = nb;
+      cur_len = nl;
+      hoff = 0;
+    }
+    if (!tiles_left && __ballot_sync(kFull, busy) == 0) break;
+  }
+  if (oth_live) flush(oth, oth_base, oth_len);
+  flush(cur, cur_base, cur_len);
+}
+
+// ------------------------------------------------------------------ degree kernels --
+
+// Number of k in [lo, hi) that also lie in [a, b).
+__device__ __forceinline__ uint64_t overlap(uint64_t lo, uint64_t hi, uint64_t a, uint64_t b) {
+  const uint64_t x = max(lo, a), y = min(hi, b);
+  return y > x ? y - x : 0;
+}
+
+// Smallest v >= 0 with v(v-1)/2 >= x.
+__device__ __forceinline__ uint64_t tri_ceil_index(uint64_t x) {
+  if (x == 0) return 0;
+  uint64_t v = static_cast<uint64_t>((1.0 + sqrt(8.0 * static_cast<double>(x) + 1.0)) * 0.5);
+  while (v > 0 && (v - 1) * (v > 1 ? v - 2 : 0) / 2 >= x) --v;  // T(v-1) >= x: step down
+  while (v * (v - 1) / 2 < x) ++v;
+  return v;
+}
+
+// counts[j] (j < node_limit) = (accumulate ? counts[j] : 0) + end points of node j among
+// edges [a, b) that are sources of non-seed edges or seed-clique edges.  Targets of
+// non-seed edges are added by the chain kernels.
+__global__ void k_degree_init(const GraphDev g, uint64_t a, uint64_t b, uint64_t node_limit,
+                              uint64_t *__restrict__ counts, int accumulate) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t j = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < node_limit;
+       j += stride) {
+    uint64_t c = accumulate ? counts[j] : 0;
+    if (j < g.n) {
+      if (j >= g.n0) {
+        const uint64_t lo = g.m0 + (j - g.n0) * g.d;
+        c += overlap(lo, lo + g.d, a, b);
+      } else {
+        // seed edges (j, u), u < j: edges j(j-1)/2 .. j(j-1)/2 + j - 1
+        const uint64_t tj = j * (j - 1) / 2;
+        c += overlap(tj, tj + j, a, b);
+        // seed edges (v, j), j < v < n0: edge v(v-1)/2 + j lies in [a, b)
+        // iff v(v-1)/2 in [a-j, b-j)
+        const uint64_t vlo = max(j + 1, a > j ? tri_ceil_index(a - j) : 0);
+        const uint64_t vhi = min(g.n0, b > j ? tri_ceil_index(b - j) : 0);
+        if (vhi > vlo) c += vhi - vlo;
+      }
+    }
+    counts[j] = c;
+  }
+}
+
+template <class RT, bool HasSeed>
+__global__ void k_degree_simple(const GraphDev g, uint64_t hit_pos, uint64_t node_limit,
+                                uint64_t *__restrict__ counts) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const RT two_m0 = seed_limit<RT>(g.two_m0);
+  for (uint64_t i = g.begin + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+       i < g.end; i += stride) {
+    RT r = static_cast<RT>(2 * i + 1);
+    do {
+      r = hash_pos<RT>(g.seed, r);
+    } while (!chain_stops<RT, HasSeed>(r, two_m0));
+    if (static_cast<uint64_t>(r) < hit_pos) {
+      const uint64_t v = target_of<RT, HasSeed>(r, g);
+      if (v < node_limit) atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
+    }
+  }
+}
+
+// Adds one end point at node v for every lane with hit set.  Nodes below `hot` go to the
+// CTA's shared-memory bins, one atomic per distinct node per warp; a bin that reaches
+// 2^31 hands 2^31 over to the global counter, so a 32-bit bin never overflows.
+__device__ __forceinline__ void histogram_add(bool hit, uint64_t v, uint32_t *bins, uint32_t hot,
+                                              uint64_t *__restrict__ counts) {
+  const bool hot_hit = hit && v < hot;
+  if (hit && !hot_hit) atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
+  const uint32_t key = hot_hit ? static_cast<uint32_t>(v) : 0xffffffffu;
+  const uint32_t peers = __match_any_sync(kFull, key);
+  if (hot_hit && (threadIdx.x & 31) == __ffs(peers) - 1) {
+    const uint32_t c = __popc(peers);
+    const uint32_t old = atomicAdd(bins + v, c);
+    if (old < 0x80000000u && old + c >= 0x80000000u) {
+      atomicSub(bins + v, 0x80000000u);
+      atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 0x80000000ull);
+    }
+  }
+}
+
+template <class RT, bool HasSeed>
+__global__ void __launch_bounds__(1024)
+k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64_t node_limit,
+                uint32_t hot, uint64_t *__restrict__ counts) {
+  extern __shared__ __align__(16) uint32_t bins[];
+  for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) bins[b] = 0;
+  __syncthreads();
+
+  const uint32_t shift = sp.tile_shift;
+  const uint32_t T = 1u << shift;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  bool first = true;
+  const RT two_m0 = seed_limit<RT>(g.two_m0);
+
+  uint64_t cur_base = 0;
+  uint32_t cur_len = 0, hoff = 0;
+  bool tiles_left = true;
+  {
+    const uint64_t t = next_tile(sp, first, gwarp);
+    if (t < sp.num_tiles) {
+      cur_base = g.begin + (t << shift);
+      cur_len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - cur_base));
+    } else {
+      tiles_left = false;
+    }
+  }
+  bool busy = false;
+  RT r = 0;
+  while (tiles_left || __any_sync(kFull, busy)) {
+    bool hit = false;
+    uint64_t v = 0;
+    if (busy) {
+      r = hash_pos<RT>(g.seed, r);
+      if (chain_stops<RT, HasSeed>(r, two_m0)) {
+        busy = false;
+        if (static_cast<uint64_t>(r) < hit_pos) {
+          v = target_of<RT, HasSeed>(r, g);
+          hit = v < node_limit;
+        }
+      }
+    }
+    if (__any_sync(kFull, hit)) histogram_add(hit, v, bins, hot, counts);
+    const uint32_t fm = __ballot_sync(kFull, !busy);
+    const uint32_t nfree = __popc(fm);
+    const uint32_t rank = __popc(fm & lt);
+    uint32_t taken = 0;
+    while (tiles_left && taken < nfree) {
+      const uint32_t avail = cur_len - hoff;
+      if (avail > 0) {
+        const uint32_t k = min(avail, nfree - taken);
+        if (!busy && rank - taken < k) {
+          r = static_cast<RT>(2 * (cur_base + hoff + (rank - taken)) + 1);
+          busy = true;
+        }
+        hoff += k;
+        taken += k;
+        continue;
+      }
+      const uint64_t t = next_tile(sp, first, gwarp);
+      if (t >= sp.num_tiles) {
+        tiles_left = false;
+        break;
+      }
+      cur_base = g.begin + (t << shift);
+      cur_len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - cur_base));
+      hoff = 0;
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
+    const uint32_t c = bins[b];
+    if (c) atomicAdd(reinterpret_cast<unsigned long long *>(counts + b), static_cast<unsigned long long>(c));
+  }
+}
+
+// ------------------------------------------------------------------------ launchers --
+
+int floor_log2(uint32_t x) { return 31 - __builtin_clz(x); }
+
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // sm_100-class opt-in limit per CTA
+
+template <class K>
+ba_status set_smem(K kernel, size_t smem) {
+  if (smem > kMaxSmemPerCta) {
+    set_error("launch shape needs more shared memory per CTA than an SM offers "
+              "(lower block or tile)");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) cudaGetLastError();  // not sticky: clear it so later checks stay exact
+  return e == cudaSuccess ? BA_OK : cuda_fail(e, "cudaFuncSetAttribute");
+}
+
+// Persistent grid: min(SMs x CTAs/SM (capped by occupancy), CTAs that have a tile).
+template <class K>
+ba_status persistent_grid(K kernel, int block, size_t smem, int ctas_per_sm, uint64_t work_ctas,
+                          int *grid) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ < 1) {
+    set_error("launch shape does not fit on an SM (block size / shared memory)");
+    return BA_ERR_INVALID_ARG;
+  }
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * std::min(occ, std::max(ctas_per_sm, 1));
+  *grid = static_cast<int>(std::max<uint64_t>(1, std::min(cap, work_ctas)));
+  return BA_OK;
+}
+
+ba_status check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
+}
+
+template <class RT, bool HasSeed>
+ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
+                     cudaStream_t stream) {
+  const uint64_t len = g.end - g.begin;
+  const int block = s.block;
+  if (s.refill == 0) {
+    int grid = 0;
+    ba_status st = persistent_grid(k_generate_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
+                                   (len + block - 1) / block, &grid);
+    if (st != BA_OK) return st;
+    k_generate_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, out);
+    g_kernel_count = 1;
+    return check_launch("k_generate_simple");
+  }
+  const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
+  const int warps = block / 32;
+  const size_t smem = static_cast<size_t>(warps) * 2 * (size_t{1} << shift) * sizeof(RT);
+  auto kernel = k_generate_refill<RT, HasSeed, false>;
+  ba_status st = set_smem(kernel, smem);
+  if (st != BA_OK) return st;
+  SchedParams sp{};
+  sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
+  sp.counter = counter;
+  sp.tile_shift = shift;
+  int grid = 0;
+  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
+  if (st != BA_OK) return st;
+  sp.total_warps = static_cast<uint32_t>(grid) * warps;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  kernel<<<grid, block, smem, stream>>>(g, BatchTable{}, sp, out);
+  g_kernel_count = 1;
+  return check_launch("k_generate_refill");
+}
+
+template <class RT, bool HasSeed>
+ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uint64_t *counts,
+                   const Shape &s, unsigned long long *counter, cudaStream_t stream) {
+  const uint64_t len = g.end - g.begin;
+  const int block = s.block;
+  if (s.refill == 0) {
+    int grid = 0;
+    ba_status st = persistent_grid(k_degree_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
+                                   (len + block - 1) / block, &grid);
+    if (st != BA_OK) return st;
+    k_degree_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, hit_pos, node_limit, counts);
+    return check_launch("k_degree_simple");
+  }
+  const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
+  const int warps = block / 32;
+  const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
+  const size_t smem = static_cast<size_t>(hot) * sizeof(uint32_t);
+  auto kernel = k_degree_refill<RT, HasSeed>;
+  ba_status st = set_smem(kernel, smem);
+  if (st != BA_OK) return st;
+  SchedParams sp{};
+  sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
+  sp.counter = counter;
+  sp.tile_shift = shift;
+  int grid = 0;
+  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
+  if (st != BA_OK) return st;
+  sp.total_warps = static_cast<uint32_t>(grid) * warps;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  kernel<<<grid, block, smem, stream>>>(g, sp, hit_pos, node_limit, hot, counts);
+  return check_launch("k_degree_refill");
+}
+
+template <class RT, bool HasSeed>
+ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, const Shape &s,
+                  unsigned long long *counter, cudaStream_t stream) {
+  const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
+  const int block = s.block;
+  const int warps = block / 32;
+  const size_t smem = static_cast<size_t>(warps) * 2 * (size_t{1} << shift) * sizeof(RT) +
+                      static_cast<size_t>(warps) * 2 * sizeof(GraphDev);
+  auto kernel = k_generate_refill<RT, HasSeed, true>;
+  ba_status st = set_smem(kernel, smem);
+  if (st != BA_OK) return st;
+  SchedParams sp{};
+  sp.num_tiles = total_tiles;
+  sp.counter = counter;
+  sp.tile_shift = shift;
+  int grid = 0;
+  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (total_tiles + warps - 1) / warps, &grid);
+  if (st != BA_OK) return st;
+  sp.total_warps = static_cast<uint32_t>(grid) * warps;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  GraphDev dummy{};
+  kernel<<<grid, block, smem, stream>>>(dummy, tab, sp, out);
+  g_kernel_count = 1;
+  return check_launch("k_generate_refill<batched>");
+}
+
+}  // namespace
+
+int last_kernel_count() { return g_kernel_count; }
+
+ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
+                          unsigned long long *counter, cudaStream_t stream) {
+  g_kernel_count = 0;
+  const bool r32 = g.end <= (1ull << 31);
+  const bool seed = g.m0 > 0;
+  if (r32) return seed ? generate_t<uint32_t, true>(g, out, s, counter, stream)
+                       : generate_t<uint32_t, false>(g, out, s, counter, stream);
+  return seed ? generate_t<uint64_t, true>(g, out, s, counter, stream)
+              : generate_t<uint64_t, false>(g, out, s, counter, stream);
+}
+
+ba_status launch_degree(const GraphDev &g_in, uint64_t node_limit, uint64_t *counts, int accumulate,
+                        const Shape &s, unsigned long long *counter, cudaStream_t stream) {
+  g_kernel_count = 0;
+  // 1. sources and seed end points, in closed form, over all node_limit entries
+  {
+    const int block = 256;
+    const uint64_t want = (node_limit + block - 1) / block;
+    const int grid = static_cast<int>(std::min<uint64_t>(want, static_cast<uint64_t>(sm_count()) * 8));
+    k_degree_init<<<std::max(grid, 1), block, 0, stream>>>(g_in, g_in.begin, g_in.end, node_limit,
+                                                           counts, accumulate);
+    ba_status st = check_launch("k_degree_init");
+    if (st != BA_OK) return st;
+    g_kernel_count = 1;
+  }
+  // 2. targets of the non-seed edges in range, by the chain of Fig. 1
+  GraphDev g = g_in;
+  g.begin = std::max(g.begin, g.m0);
+  if (g.begin >= g.end) return BA_OK;
+  // A chain that stops at an even position r >= 2 m0 names node n0 + (r/2 - m0)/d, which is
+  // below node_limit iff r < 2 m0 + 2 (node_limit - n0) d; seed positions may always hit.
+  uint64_t hit_pos = g.two_m0;
+  if (node_limit > g.n0) {
+    const unsigned __int128 hp = static_cast<unsigned __int128>(g.two_m0) +
+                                 static_cast<unsigned __int128>(2) * (node_limit - g.n0) * g.d;
+    hit_pos = hp > (static_cast<unsigned __int128>(1) << 63) ? (1ull << 63) : static_cast<uint64_t>(hp);
+  }
+  const bool r32 = g.end <= (1ull << 31);
+  const bool seed = g.m0 > 0;
+  ba_status st;
+  if (r32) st = seed ? degree_t<uint32_t, true>(g, hit_pos, node_limit, counts, s, counter, stream)
+                     : degree_t<uint32_t, false>(g, hit_pos, node_limit, counts, s, counter, stream);
+  else st = seed ? degree_t<uint64_t, true>(g, hit_pos, node_limit, counts, s, counter, stream)
+                 : degree_t<uint64_t, false>(g, hit_pos, node_limit, counts, s, counter, stream);
+  if (st == BA_OK) g_kernel_count = 2;
+  return st;
+}
+
+ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,
+                       int64_t *out, const Shape &s, unsigned long long *counter, cudaStream_t stream) {
+  g_kernel_count = 0;
+  if (total_tiles == 0) return BA_OK;
+  if (r32) return has_seed ? batch_t<uint32_t, true>(tab, total_tiles, out, s, counter, stream)
+                           : batch_t<uint32_t, false>(tab, total_tiles, out, s, counter, stream);
+  return has_seed ? batch_t<uint64_t, true>(tab, total_tiles, out, s, counter, stream)
+                  : batch_t<uint64_t, false>(tab, total_tiles, out, s, counter, stream);
+}
+
+}  // namespace ba

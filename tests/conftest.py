@@ -10,3 +10,19 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
     config.addinivalue_line("markers", "slow: longer CPU test (still part of the CPU suite)")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def ba():
+    """The CUDA library's Python binding (built first; fails loudly when CUDA is missing)."""
+    import torch
+
+    from paper_1602_07106_gb300 import build as ba_build
+    ba_build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_1602_07106_gb300 import ba as module
+    return module

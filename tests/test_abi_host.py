@@ -1,0 +1,110 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads, exports every
+function include/ba.h declares, and rejects malformed arguments before touching a GPU."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1602_07106_gb300 import build as ba_build
+
+LIB = ba_build.build()  # nvcc cross-compiles sm_103a without a GPU
+from paper_1602_07106_gb300 import ba  # noqa: E402  (needs the built library)
+
+
+def test_every_declared_function_is_exported():
+    names = ba.declared_functions()
+    assert len(names) >= 25
+    lib = ctypes.CDLL(LIB)
+    missing = [nm for nm in names if not hasattr(lib, nm)]
+    assert not missing, missing
+
+
+def test_library_targets_sm_103a_only():
+    # the build passes exactly one -gencode (sm_103a); the binding loads that file
+    assert ba_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.samefile(ba.LIB_PATH, LIB)
+
+
+def test_num_edges_and_status_strings():
+    assert ba.ba_num_edges(10**6, 4, 0) == 4 * 10**6
+    assert ba.ba_num_edges(2**27, 16) == 2**31
+    assert ba.ba_num_edges(10**10, 100) == 10**12
+    assert ba.ba_num_edges(10, 3, 4) == 6 + 18
+    assert ba.ba_num_edges(10, 0, 0) == 0
+    assert ba.ba_num_edges(10, 1, 11) == 0
+    assert ba.ba_num_edges(2**62 + 1, 1, 0) == 0
+    assert ba.ba_status_string(0) == "ok"
+    assert ba.ba_status_string(2).startswith("edge range")
+    assert ba.ba_version() >= 10000
+
+
+@pytest.mark.parametrize("args,status", [
+    ((1, 10, 0, 0, 0, 1), ba.BA_ERR_INVALID_ARG),        # d = 0
+    ((1, 0, 1, 0, 0, 0), ba.BA_ERR_INVALID_ARG),         # n = 0
+    ((1, 10, 1, 11, 0, 1), ba.BA_ERR_INVALID_ARG),       # n0 > n
+    ((1, 10, 1, 0, 0, 11), ba.BA_ERR_RANGE),             # end > m
+    ((1, 10, 1, 0, 5, 4), ba.BA_ERR_RANGE),              # begin > end
+    ((1, 2**62, 2, 0, 0, 1), ba.BA_ERR_OVERFLOW),        # m > 2^62
+])
+def test_generate_rejects_bad_arguments_before_any_launch(args, status):
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_edges(*args, out=0x1000, stream=0)
+    assert e.value.status == status
+
+
+def test_generate_rejects_null_or_misaligned_output_and_accepts_empty_range():
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_edges(1, 10, 1, 0, 0, 5, out=None, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_edges(1, 10, 1, 0, 0, 5, out=0x1008, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    ba.ba_generate_edges(1, 10, 1, 0, 3, 3, out=None, stream=0)   # empty: no launch, OK
+
+
+def test_degree_count_argument_rules():
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_degree_count_range(1, 10, 1, 0, 0, 11, 5, counts=0x1000, stream=0)
+    assert e.value.status == ba.BA_ERR_RANGE
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_degree_count_range(1, 10, 1, 0, 0, 10, 5, counts=0x1004, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    ba.ba_degree_count(1, 10, 1, 0, counts=None, stream=0)          # node_limit 0: no-op
+
+
+def test_tuning_overrides_validate_and_round_trip(tmp_path):
+    default = ba.ba_get_tuning(ba.BA_KIND_GENERATE)
+    assert default["block"] % 32 == 0 and default["tile"] & (default["tile"] - 1) == 0
+    for bad in ({"block": 100, "refill": 1}, {"tile": 100, "refill": 1}, {"refill": 3},
+                {"block": 2048, "refill": 1}):
+        with pytest.raises(ba.BAError):
+            ba.ba_set_tuning(ba.BA_KIND_GENERATE, bad)
+    ba.ba_set_tuning(ba.BA_KIND_GENERATE, {"block": 128, "ctas_per_sm": 8, "tile": 1024,
+                                           "refill": 1})
+    assert ba.ba_get_tuning(ba.BA_KIND_GENERATE)["tile"] == 1024
+    ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
+    assert ba.ba_get_tuning(ba.BA_KIND_GENERATE) == default
+    path = tmp_path / "tune.json"
+    path.write_text('{"sm_count": 152, "entries": [\n  {"kind": 1, "r32": 0, "block": 256, '
+                    '"ctas_per_sm": 4, "tile": 256, "refill": 1, "hist_bins": 8192}\n]}\n')
+    ba.ba_tune_load(str(path))
+    assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["hist_bins"] == 8192
+    out = tmp_path / "saved.json"
+    ba.ba_tune_save(str(out))
+    assert '"hist_bins": 8192' in out.read_text()
+    with pytest.raises(ba.BAError):
+        ba.ba_tune_load(str(tmp_path / "missing.json"))
+
+
+def test_batch_and_server_argument_rules():
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_batch_plan_create([(1, 10, 0, 0, 0, 5)])                  # d = 0
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_batch([(1, 10, 1, 0, 0, 11)], out=0x1000, stream=0)
+    assert e.value.status == ba.BA_ERR_RANGE
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_batch([(1, 10, 1, 0, 0, 5), (2, 10, 1, 0, 0, 5)], out=0x1000,
+                             offsets=[0, 4, 9], stream=0)               # graph 0 does not fit
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    ba.ba_generate_batch([], out=None, stream=0)                         # nothing to do

@@ -1,0 +1,126 @@
+"""GPU parity of ba_generate_edges (Fig. 1 over edge ranges) against the oracle.
+
+Integer work: every comparison is bit-exact.  Sizes span many warp tiles with ragged
+tails; the full 2^31-edge graph is generated in the launch shape the benchmark uses and
+checked on oracle-computed ranges at its start, middle and end, plus properties that hold
+at any size (the source column is n0 + floor((i-m0)/d); targets never exceed sources).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import parallel as opar
+from paper_1602_07106_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(ba, seed, n, d, n0, a, b):
+    out = torch.empty((b - a, 2), dtype=torch.int64, device="cuda")
+    ba.ba_generate_edges(seed, n, d, n0, a, b, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_small_workload_full_edge_list_bit_exact(ba):
+    g = W.PLAIN_SMALL
+    E = oracle.bb_array(g.seed, g.n, g.d, g.n0).reshape(-1, 2)
+    got = ba.generate_edges(g.seed, g.n, g.d).cpu().numpy()
+    np.testing.assert_array_equal(got, E)
+
+
+CASES = [
+    (1, 1, 1, 0, 0, 1), (1, 2, 1, 0, 0, 2), (3, 1000, 1, 0, 0, 1000),
+    (5, 777, 7, 0, 0, 777 * 7), (9, 5000, 3, 0, 17, 14_983), (11, 40_000, 2, 0, 1, 79_999),
+    (13, 1000, 4, 5, 0, 10 + 995 * 4), (15, 3000, 2, 3, 2, 5000), (17, 500, 32, 33, 0, 528 + 467 * 32),
+    (19, 200, 5, 1, 0, 995), (21, 64, 1, 2, 0, 63), (23, 40, 3, 40, 0, 780), (25, 40, 3, 40, 100, 700),
+    (27, 100_000, 13, 0, 123_457, 987_654), (2**63 + 5, 10_000, 16, 17, 0, 136 + 9983 * 16),
+    (29, 4, 2**31 + 3, 0, 0, 4 * (2**31 + 3)),       # d above 2^31 (all four nodes)
+]
+
+
+@pytest.mark.parametrize("seed,n,d,n0,a,b", CASES)
+def test_ranges_match_oracle(ba, seed, n, d, n0, a, b):
+    if b - a > 3_000_000:
+        a = b - 3_000_000
+    np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
+                                  opar.edges_range(seed, n, d, n0, a, b))
+
+
+def test_empty_range_and_single_edges(ba):
+    out = torch.full((4, 2), -7, dtype=torch.int64, device="cuda")
+    ba.ba_generate_edges(1, 100, 2, 0, 50, 50, out)
+    torch.cuda.synchronize()
+    assert (out == -7).all()
+    for i in (0, 1, 63, 64, 65, 199):
+        np.testing.assert_array_equal(_gpu(ba, 4, 100, 2, 0, i, i + 1),
+                                      oracle.edges_range(4, 100, 2, 0, i, i + 1))
+
+
+SHAPES = [
+    {"refill": 0, "block": 256, "ctas_per_sm": 8},
+    {"refill": 0, "block": 32, "ctas_per_sm": 1},
+    {"refill": 1, "block": 32, "ctas_per_sm": 1, "tile": 64},
+    {"refill": 1, "block": 128, "ctas_per_sm": 2, "tile": 256},
+    {"refill": 1, "block": 256, "ctas_per_sm": 4, "tile": 512},
+    {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 1024},
+    {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 512},
+    {"refill": 1, "block": 64, "ctas_per_sm": 16, "tile": 4096},
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "-".join(f"{k}{v}" for k, v in s.items()))
+def test_output_does_not_depend_on_launch_shape(ba, shape):
+    # section 2: the graph depends only on the hash, not on how the work is split
+    cases = [(31, 300_000, 3, 0, 5, 899_999), (37, 50_000, 6, 7, 0, 21 + 49_993 * 6)]
+    try:
+        ba.ba_set_tuning(ba.BA_KIND_GENERATE, shape)
+        for seed, n, d, n0, a, b in cases:
+            np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
+                                          opar.edges_range(seed, n, d, n0, a, b))
+    finally:
+        ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
+
+
+def test_64_bit_positions_far_into_a_large_graph(ba):
+    # m = 2^33: positions above 2^32 take the 64-bit path
+    n, d = 2**29, 16
+    m = n * d
+    for a, b in [(m - 300_000, m), (2**31 - 1000, 2**31 + 150_000), (2**32 - 777, 2**32 + 777)]:
+        np.testing.assert_array_equal(_gpu(ba, 77, n, d, 0, a, b),
+                                      opar.edges_range(77, n, d, 0, a, b))
+
+
+def test_host_output_matches_device_output(ba):
+    g = W.PLAIN_SMALL
+    host = torch.empty((g.m, 2), dtype=torch.int64).pin_memory()
+    ba.ba_generate_edges_host(g.seed, g.n, g.d, 0, 0, g.m, host)
+    dev = ba.generate_edges(g.seed, g.n, g.d).cpu()
+    assert torch.equal(host, dev)
+    # several chunks and a ragged tail
+    n, d = 2**26, 1
+    a, b = 3, 2**26 - 5
+    host2 = torch.empty((b - a, 2), dtype=torch.int64)
+    ba.ba_generate_edges_host(99, n, d, 0, a, b, host2)
+    for lo, hi in [(0, 100_000), (2**25 - 50_000, 2**25 + 50_000), (b - a - 100_000, b - a)]:
+        np.testing.assert_array_equal(host2[lo:hi].numpy(),
+                                      oracle.edges_range(99, n, d, 0, a + lo, a + hi))
+
+
+def test_large_workload_full_size_spot_ranges_and_properties(ba):
+    g = W.PLAIN_LARGE
+    out = torch.empty((g.m, 2), dtype=torch.int64, device="cuda")
+    ba.ba_generate_edges(g.seed, g.n, g.d, 0, 0, g.m, out)
+    torch.cuda.synchronize()
+    for a, b in W.PLAIN_LARGE_SPOT_RANGES:
+        np.testing.assert_array_equal(out[a:b].cpu().numpy(),
+                                      opar.edges_range(g.seed, g.n, g.d, 0, a, b))
+    step = 2**27
+    for a in range(0, g.m, step):
+        blk = out[a:a + step]
+        i = torch.arange(a, a + blk.shape[0], device="cuda", dtype=torch.int64)
+        assert torch.equal(blk[:, 0], i // g.d)
+        assert bool((blk[:, 1] <= blk[:, 0]).all()) and bool((blk[:, 1] >= 0).all())
+    del out
+    torch.cuda.empty_cache()

@@ -1,0 +1,104 @@
+"""GPU tests of the serving loop: each served result is bit-identical to the plain call
+(and to the oracle), alone and in a mix of concurrent requests; admission respects the
+memory budget without hanging."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1602_07106_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _plain(ba, seed, n, d, n0, a, b):
+    out = torch.empty((b - a, 2), dtype=torch.int64, device="cuda")
+    ba.ba_generate_edges(seed, n, d, n0, a, b, out)
+    torch.cuda.synchronize()
+    return out
+
+
+def _requests():
+    trace = W.serving_trace(rate=2000.0, duration=0.02, trace_seed=11, len_hi=3e6)
+    reqs = [(r.graph.seed, r.graph.n, r.graph.d, 0, r.edge_begin, r.edge_end) for r in trace]
+    reqs += [(5, 1000, 3, 4, 0, 2995), (6, 2**29, 16, 0, 2**33 - 100_000, 2**33), (7, 10, 1, 0, 3, 3)]
+    return reqs
+
+
+def test_served_results_equal_plain_alone_and_in_mix(ba):
+    reqs = _requests()
+    assert len(reqs) >= 20
+    srv = ba.ba_server_create(memory_budget_bytes=4 << 30, chunk_edges=1 << 20, max_active=64)
+    try:
+        alone = []
+        for r in reqs:
+            t = ba.ba_server_submit(srv, *r)
+            ba.ba_server_wait(srv, t, 60_000)
+            alone.append(ba.server_result_tensor(srv, t))
+            ba.ba_server_release(srv, t)
+        tickets = [ba.ba_server_submit(srv, *r) for r in reqs]
+        mixed = []
+        for t in tickets:
+            ba.ba_server_wait(srv, t, 60_000)
+            state, lat = ba.ba_server_poll(srv, t)
+            assert state == ba.BA_REQ_DONE and lat >= 0
+            mixed.append(ba.server_result_tensor(srv, t))
+        torch.cuda.synchronize()
+        for t in tickets:
+            ba.ba_server_release(srv, t)
+        stats = ba.ba_server_stats_get(srv)
+        assert stats["completed"] == 2 * len(reqs) and stats["bytes_in_use"] == 0
+    finally:
+        ba.ba_server_destroy(srv)
+    for k, r in enumerate(reqs):
+        want = _plain(ba, *r)
+        assert torch.equal(alone[k], want), k
+        assert torch.equal(mixed[k], want), k
+        if k % 7 == 0 and r[5] > r[4]:
+            a = r[4]
+            b = min(r[5], a + 200_000)
+            np.testing.assert_array_equal(mixed[k][:b - a].cpu().numpy(), oracle.edges_range(r[0], r[1], r[2], r[3], a, b))
+
+
+def test_admission_waits_for_memory_and_never_hangs(ba):
+    # budget for two 1M-edge requests: the third stays queued until one is released
+    srv = ba.ba_server_create(memory_budget_bytes=2 * 16 * 2**20, chunk_edges=1 << 18, max_active=8)
+    try:
+        ts = [ba.ba_server_submit(srv, 100 + k, 2**22, 4, 0, 0, 2**20) for k in range(3)]
+        ba.ba_server_wait(srv, ts[0], 60_000)
+        ba.ba_server_wait(srv, ts[1], 60_000)
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_wait(srv, ts[2], 300)
+        assert e.value.status == ba.BA_ERR_TIMEOUT
+        assert ba.ba_server_poll(srv, ts[2])[0] == ba.BA_REQ_QUEUED
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_release(srv, ts[2])                 # not done yet
+        assert e.value.status == ba.BA_ERR_BUSY
+        ba.ba_server_release(srv, ts[0])
+        ba.ba_server_wait(srv, ts[2], 60_000)
+        got = ba.server_result_tensor(srv, ts[2])
+        assert torch.equal(got, _plain(ba, 102, 2**22, 4, 0, 0, 2**20))
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_submit(srv, 1, 2**22, 4, 0, 0, 2**21 + 1)   # larger than the budget
+        assert e.value.status == ba.BA_ERR_NOMEM
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_poll(srv, 10**9)
+        assert e.value.status == ba.BA_ERR_NOT_FOUND
+    finally:
+        ba.ba_server_destroy(srv)
+
+
+def test_autotuner_picks_a_valid_shape_and_output_is_unchanged(ba):
+    n, d = 2**20, 8
+    m = n * d
+    scratch = torch.empty((m, 2), dtype=torch.int64, device="cuda")
+    before = _plain(ba, 3, n, d, 0, 0, m).clone()
+    shape = ba.ba_tune(ba.BA_KIND_GENERATE, 3, n, d, 0, m, scratch)
+    assert shape["block"] % 32 == 0
+    assert ba.ba_get_tuning(ba.BA_KIND_GENERATE, m) == shape
+    assert torch.equal(_plain(ba, 3, n, d, 0, 0, m), before)
+    dshape = ba.ba_tune(ba.BA_KIND_DEGREE, 3, n, d, 0, m)
+    assert dshape["block"] % 32 == 0
+    bshape = ba.ba_tune(ba.BA_KIND_BATCH, 3, n, d, 0, m, scratch)
+    assert bshape["block"] % 32 == 0
+    assert torch.equal(_plain(ba, 3, n, d, 0, 0, m), before)
