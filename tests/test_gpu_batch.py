@@ -74,7 +74,7 @@ def test_batch_ranges_gaps_and_64_bit_graphs_equal_plain_calls(ba):
 
 
 @pytest.mark.parametrize("shape", [{"refill": 1, "block": 64, "ctas_per_sm": 2, "tile": 64},
-                                   {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 2048}])
+                                   {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 1024}])
 def test_batch_output_does_not_depend_on_shape(ba, shape):
     table = W.batch_table(G=64, n_lo=1e2, n_hi=1e4, table_seed=3)
     graphs = [(g.seed, g.n, g.d, g.n0, 0, g.m) for g in table]
@@ -93,8 +93,8 @@ def test_batch_workload_first_wave_exact(ba):
     table = W.batch_table()
     graphs, total = [], 0
     for g in table:
-        if total + g.m > 8 * 2**30 // 16:
-            break
+        if total + g.m > 8 * 2**30 // 16 or len(graphs) == 96:
+            continue
         graphs.append((g.seed, g.n, g.d, g.n0, 0, g.m))
         total += g.m
     assert len(graphs) >= 16

@@ -21,7 +21,7 @@ def _plain(ba, seed, n, d, n0, a, b):
 def _requests():
     trace = W.serving_trace(rate=2000.0, duration=0.02, trace_seed=11, len_hi=3e6)
     reqs = [(r.graph.seed, r.graph.n, r.graph.d, 0, r.edge_begin, r.edge_end) for r in trace]
-    reqs += [(5, 1000, 3, 4, 0, 2995), (6, 2**29, 16, 0, 2**33 - 100_000, 2**33), (7, 10, 1, 0, 3, 3)]
+    reqs += [(5, 1000, 3, 4, 0, 2994), (6, 2**29, 16, 0, 2**33 - 100_000, 2**33), (7, 10, 1, 0, 3, 3)]
     return reqs
 
 
