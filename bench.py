@@ -46,10 +46,56 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="main step only")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--cpu-sample-edges", type=int, default=2**25)
+    ap.add_argument("--cpu-sample-edges", type=int, default=2**28)
+    ap.add_argument("--profile", choices=["generate", "degree", "batch"], default=None,
+                    help="run a small case of one kernel (for ncu captures) and exit")
+    ap.add_argument("--profile-edges", type=int, default=2**26)
+    ap.add_argument("--profile-reps", type=int, default=3)
     return ap.parse_args()
+
+
+def profile_case(args):
+    """A few launches of one kernel on a small slice of the large workload: edges
+    [0, profile_edges) of n = 2^27, d = 16, seed 42 (1 GB of output at the default 2^26,
+    larger than L2), for ncu."""
+    import torch
+
+    from paper_1602_07106_gb300 import build as ba_build
+    ba_build.build()
+    from paper_1602_07106_gb300 import ba
+    g = W.PLAIN_LARGE
+    e = args.profile_edges
+    stream = torch.cuda.current_stream()
+    if args.profile == "generate":
+        out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
+        for _ in range(args.profile_reps):
+            ba.ba_generate_edges(g.seed, g.n, g.d, 0, 0, e, out, stream)
+    elif args.profile == "degree":
+        counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+        for _ in range(args.profile_reps):
+            ba.ba_degree_count_range(g.seed, g.n, g.d, 0, 0, e, NODE_LIMIT, counts, 0, stream)
+    else:
+        table = W.batch_table()
+        graphs, total = [], 0
+        for gg in table:
+            if total + gg.m > e:
+                continue
+            graphs.append((gg.seed, gg.n, gg.d, gg.n0, 0, gg.m))
+            total += gg.m
+        out = torch.empty((total, 2), dtype=torch.int64, device="cuda")
+        plan = ba.ba_batch_plan_create(graphs)
+        try:
+            for _ in range(args.profile_reps):
+                ba.ba_batch_plan_launch(plan, out, stream)
+            torch.cuda.synchronize()
+        finally:
+            ba.ba_batch_plan_destroy(plan)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "edges": e, "reps": args.profile_reps}))
+    return 0
 
 
 def env_rank():
@@ -379,7 +425,7 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
         result["extras"] = extras(args, ba, torch, stream, result)
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_leg(20.0, args.cpu_sample_edges)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -516,6 +562,8 @@ def serving(args, ba, torch, plain_rate):
 
 def main():
     args = parse_args()
+    if args.profile:
+        return profile_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     return gpu_arm(args)
