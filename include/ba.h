@@ -205,6 +205,33 @@ ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
                             const int64_t *offsets_host, int64_t *out_dev,
                             const ba_tuning *tune, void *stream);
 
+/* ------------------------------------------- batched generation without allocation -- */
+
+/*
+ * The paper has no counterpart to this call; it is an interface variant for callers that
+ * cannot allocate device memory when they want edges -- for example code running while
+ * another framework's caching allocator owns all device memory, hosts whose fixed device
+ * memory budget forbids hidden allocations, or code that must not risk an allocation
+ * failure or the synchronisation an allocation can cause in the middle of its stream.
+ *
+ * Same result as ba_generate_batch (same arguments, default launch shape), but the call
+ * allocates nothing: no cudaMalloc, cudaFree or stream-ordered allocation.  Its scratch
+ * (the per-graph constant table, the tile prefix and the tile counter) lives in one static
+ * device array of about 114 KB that every GPU loading libba holds until the process exits.
+ *  - At most BA_NOALLOC_MAX_GRAPHS graphs per call; a larger G returns BA_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - The descriptor table is copied from host memory on `stream`; a copy from pageable
+ *    memory waits for the work already on `stream`.  The tile counter is cleared on every
+ *    call; the tables are rewritten in full.
+ *  - Every call shares the one array and it keeps the previous call's contents: calls whose
+ *    device work overlaps (other streams, other host threads) race; serialise them.
+ */
+#define BA_NOALLOC_MAX_GRAPHS 1024
+ba_status ba_generate_batch_noalloc(const ba_graph_desc *descs, int32_t G,
+                                    const int64_t *offsets_host, int64_t *out_dev,
+                                    void *stream);
+
 /* ------------------------------------------------- serving (continuous batching) -- */
 
 typedef struct ba_server ba_server;

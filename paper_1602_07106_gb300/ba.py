@@ -86,6 +86,8 @@ _sig("ba_batch_plan_launch", ctypes.c_int, _vp, _vp, _vp)
 _sig("ba_batch_plan_destroy", ctypes.c_int, _vp)
 _sig("ba_generate_batch", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp, _vp,
      ctypes.POINTER(ba_tuning), _vp)
+_sig("ba_generate_batch_noalloc", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp, _vp,
+     _vp)
 _sig("ba_server_create", ctypes.c_int, ctypes.POINTER(ba_server_config), ctypes.POINTER(_vp))
 _sig("ba_server_submit", ctypes.c_int, _vp, ctypes.POINTER(ba_graph_desc), ctypes.POINTER(_u64))
 _sig("ba_server_poll", ctypes.c_int, _vp, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_u64))
@@ -269,6 +271,19 @@ def ba_generate_batch(graphs, out, offsets=None, tune=None, stream=None) -> None
     t = _tuning(tune)
     _check(_lib.ba_generate_batch(arr, G, off, _ptr(out), ctypes.byref(t) if t is not None else None,
                                   _stream(stream)), "ba_generate_batch")
+
+
+BA_NOALLOC_MAX_GRAPHS = 1024
+
+
+def ba_generate_batch_noalloc(graphs, out, offsets=None, stream=None) -> None:
+    """ba_generate_batch without any device allocation: scratch comes from the library's
+    static device table (at most BA_NOALLOC_MAX_GRAPHS graphs); calls that overlap on the
+    GPU share that table and must be serialised by the caller."""
+    arr, G = _descs(graphs)
+    keep, off = _offsets_arg(offsets)
+    _check(_lib.ba_generate_batch_noalloc(arr, G, off, _ptr(out), _stream(stream)),
+           "ba_generate_batch_noalloc")
 
 
 def ba_server_create(memory_budget_bytes=0, chunk_edges=0, max_active=0, max_inflight_ticks=0,
