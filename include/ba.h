@@ -121,14 +121,17 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
  *  tile         edges per warp tile (power of two, 64..4096)
  *  refill       0 = one thread per edge, no refill (the simple kernel);
  *               1 = warp refill every hash step (ballot/popc compaction)
- *  hist_bins    degree kernel: shared-memory histogram bins per CTA */
+ *  hist_bins    degree kernel: shared-memory histogram bins per CTA
+ *  hist_agg     degree kernel: 1 = one shared-memory atomic per distinct node per warp
+ *               (__match_any_sync aggregation), 0 = one atomic per hitting lane */
 typedef struct ba_tuning {
     int32_t block;
     int32_t ctas_per_sm;
     int32_t tile;
     int32_t refill;
     int32_t hist_bins;
-    int32_t reserved[3];
+    int32_t hist_agg;
+    int32_t reserved[2];
 } ba_tuning;
 
 /* Kernel families the tuner keys on. */

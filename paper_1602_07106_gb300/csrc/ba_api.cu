@@ -79,6 +79,7 @@ GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint
                         uint64_t end) {
   GraphDev g{};
   g.seed = seed;
+  g.seed_pre = seed_premix(seed);
   g.n = n;
   g.n0 = n0;
   g.m0 = n0 > 0 ? n0 * (n0 - 1) / 2 : 0;
@@ -92,7 +93,6 @@ GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint
   const unsigned __int128 one = 1;
   g.div.l = l;
   g.div.m64 = static_cast<uint64_t>(((one << (62 + l)) + d - 1) / d);
-  g.div.p32 = 31 + l;
   g.div.m32 = static_cast<uint32_t>(((one << (31 + l)) + d - 1) / d);
   return g;
 }

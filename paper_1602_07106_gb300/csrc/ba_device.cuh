@@ -38,6 +38,44 @@ __device__ __forceinline__ uint64_t hash_r64(uint64_t seed, uint64_t r) {
   return __umul64hi(mix64(seed ^ (r * kGamma)), r);
 }
 
+// The seed's share of the first xor-shift.  Logical shifts distribute over xor, so for
+// x = seed ^ p:  x ^ (x >> 30) = (seed ^ (seed >> 30)) ^ p ^ (p >> 30), and
+// seed_pre = seed ^ (seed >> 30) is a per-graph constant.
+__host__ __device__ constexpr uint64_t seed_premix(uint64_t seed) { return seed ^ (seed >> 30); }
+
+// h(r) with seed_pre in place of the seed: one xor fewer per hash than the plain form.
+// On sm_103 the hash is bound by the IMAD pipe (the 64-bit multiplies), so this is the
+// form the hot loops use; the simple kernels keep the plain form as a cross-check.
+__device__ __forceinline__ uint32_t hash_r32_pre(uint64_t seed_pre, uint32_t r) {
+  const uint64_t p = static_cast<uint64_t>(r) * kGamma;
+  uint64_t z = (seed_pre ^ p ^ (p >> 30)) * kMixA;
+  z = (z ^ (z >> 27)) * kMixB;
+  z ^= z >> 31;
+  const uint32_t zlo = static_cast<uint32_t>(z);
+  const uint32_t zhi = static_cast<uint32_t>(z >> 32);
+  const uint32_t t = __umulhi(zlo, r);
+  return static_cast<uint32_t>((static_cast<uint64_t>(zhi) * r + t) >> 32);
+}
+
+__device__ __forceinline__ uint64_t hash_r64_pre(uint64_t seed_pre, uint64_t r) {
+  const uint64_t p = r * kGamma;
+  uint64_t z = (seed_pre ^ p ^ (p >> 30)) * kMixA;
+  z = (z ^ (z >> 27)) * kMixB;
+  z ^= z >> 31;
+  return __umul64hi(z, r);
+}
+
+template <class RT>
+__device__ __forceinline__ RT hash_pre(uint64_t seed_pre, RT r);
+template <>
+__device__ __forceinline__ uint32_t hash_pre<uint32_t>(uint64_t seed_pre, uint32_t r) {
+  return hash_r32_pre(seed_pre, r);
+}
+template <>
+__device__ __forceinline__ uint64_t hash_pre<uint64_t>(uint64_t seed_pre, uint64_t r) {
+  return hash_r64_pre(seed_pre, r);
+}
+
 template <class RT>
 __device__ __forceinline__ RT hash_pos(uint64_t seed, RT r);
 template <>
@@ -52,21 +90,21 @@ __device__ __forceinline__ uint64_t hash_pos<uint64_t>(uint64_t seed, uint64_t r
 // Division by the constant d (Granlund & Montgomery 1994, multiply-high by a rounded-up
 // reciprocal).  With l = ceil(log2 d):
 //   64-bit numerators x < 2^62:  M = ceil(2^(62+l)/d) < 2^64,  x/d = umulhi(4x, M) >> l
-//   31-bit numerators x < 2^31:  M = ceil(2^(31+l)/d) < 2^32,  x/d = (x*M) >> (31+l)
+//   31-bit numerators x < 2^31:  M = ceil(2^(31+l)/d) < 2^32,  x/d = umulhi(x, M) >> (l-1)
+//                                (d = 1, l = 0: x itself)
 // Exact because x*(M*d - 2^p) < 2^p in both cases.
 struct FastDiv {
   uint64_t m64;
   uint32_t l;
   uint32_t m32;
-  uint32_t p32;
-  uint32_t pad;
+  uint32_t pad[2];
 };
 
 __device__ __forceinline__ uint64_t div64(uint64_t x, const FastDiv &f) {
   return __umul64hi(x << 2, f.m64) >> f.l;
 }
 __device__ __forceinline__ uint32_t div32(uint32_t x, const FastDiv &f) {
-  return static_cast<uint32_t>((static_cast<uint64_t>(x) * f.m32) >> f.p32);
+  return f.l ? __umulhi(x, f.m32) >> (f.l - 1) : x;
 }
 
 // Seed clique (section 4): position p < 2 m0 belongs to seed edge k = p/2 = v(v-1)/2 + u,
@@ -83,6 +121,7 @@ __device__ __forceinline__ uint64_t clique_position(uint64_t p) {
 // Per-graph constants, computed on the host (make_graph_dev in ba_api.cu).
 struct GraphDev {
   uint64_t seed;
+  uint64_t seed_pre;  // seed_premix(seed)
   uint64_t n;         // nodes
   uint64_t n0;        // first non-seed node
   uint64_t m0;        // seed edges

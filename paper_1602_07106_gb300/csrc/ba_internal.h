@@ -16,6 +16,8 @@ struct SchedParams {
   unsigned long long *counter;   // zeroed before the launch; tiles past the first wave
   uint32_t tile_shift;
   uint32_t total_warps;          // warps in the grid (first tile of warp w is w)
+  uint32_t hist_agg;             // degree kernel: warp-aggregate histogram increments
+  uint32_t pad;
 };
 
 // Graph table of a batched launch (device pointers).
@@ -31,6 +33,7 @@ struct Shape {
   int tile = 0;
   int refill = 1;
   int hist_bins = 0;
+  int hist_agg = 0;
 };
 
 // ---- host helpers (ba_api.cu)

@@ -84,17 +84,40 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
                                            const GraphDev &g, int64_t *__restrict__ out) {
   __syncwarp();
   const uint64_t out0 = g.out_edge + (base - g.begin);
-  for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
-    const uint64_t i = base + j;
-    uint64_t u, v;
-    if (HasSeed && i < g.m0) {
-      u = clique_position(2 * i);
-      v = clique_position(2 * i + 1);
-    } else {
-      u = source_of<RT, HasSeed>(i, g);
-      v = target_of<RT, HasSeed>(stage[j], g);
+  if constexpr (sizeof(RT) == 4) {
+    // 32-bit positions: i < 2^31 and every node ID < 2^32, so the pairs are built from
+    // 32-bit words (high words zero).
+    const uint32_t n0 = static_cast<uint32_t>(g.n0);
+    const uint32_t m0 = static_cast<uint32_t>(g.m0);
+    const uint32_t b32 = static_cast<uint32_t>(base);
+    int4 *dst = reinterpret_cast<int4 *>(out) + out0;
+    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+      const uint32_t i = b32 + j;
+      uint32_t u, v;
+      if (HasSeed && i < g.m0) {
+        u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
+        v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
+      } else {
+        const uint32_t r = stage[j];
+        u = n0 + div32(i - m0, g.div);
+        v = (HasSeed && r < g.two_m0) ? static_cast<uint32_t>(clique_position(r))
+                                      : n0 + div32((r >> 1) - m0, g.div);
+      }
+      __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
     }
-    store_edge(out, out0 + j, u, v);
+  } else {
+    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+      const uint64_t i = base + j;
+      uint64_t u, v;
+      if (HasSeed && i < g.m0) {
+        u = clique_position(2 * i);
+        v = clique_position(2 * i + 1);
+      } else {
+        u = source_of<RT, HasSeed>(i, g);
+        v = target_of<RT, HasSeed>(stage[j], g);
+      }
+      store_edge(out, out0 + j, u, v);
+    }
   }
   __syncwarp();
 }
@@ -148,24 +171,60 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   uint32_t cur_len = 0, oth_len = 0, hoff = 0;
   bool oth_live = false, tiles_left = true;
   if (!fetch(cur, cur_base, cur_len)) return;
+  // What a lane needs to start edge cur_base + o: position r = cur_r0 + 2o, stage slot
+  // cur_s0 + o, and (batched) the seed and seed size of the tile's graph.
+  RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
+  uint32_t cur_s0 = static_cast<uint32_t>(cur) << shift;
+  uint64_t cur_spre = g0.seed_pre;
+  RT cur_2m0 = seed_limit<RT>(g0.two_m0);
+  if constexpr (Batched) {
+    cur_spre = sg[cur].seed_pre;
+    cur_2m0 = seed_limit<RT>(sg[cur].two_m0);
+  }
 
   // Lane state.
   bool busy = false;
   RT r = 0;
   uint32_t sidx = 0;
-  uint64_t lseed = g0.seed;
-  RT l2m0 = seed_limit<RT>(g0.two_m0);
+  uint64_t lspre = cur_spre;
+  RT l2m0 = cur_2m0;
+  bool fast = false;
+
+  // Fast step: every lane is busy and the current tile still has >= 32 IDs to hand out,
+  // so each lane whose chain stops parks r and starts the next ID at once.
+  auto fast_step = [&]() {
+    r = hash_pre<RT>(lspre, r);
+    const bool stop = chain_stops<RT, HasSeed>(r, l2m0);
+    if (stop) stage[sidx] = r;
+    const uint32_t fm = __ballot_sync(kFull, stop);
+    if (stop) {
+      const uint32_t o = hoff + __popc(fm & lt);
+      sidx = cur_s0 + o;
+      r = cur_r0 + 2 * static_cast<RT>(o);
+      if constexpr (Batched) {
+        lspre = cur_spre;
+        l2m0 = cur_2m0;
+      }
+    }
+    hoff += __popc(fm);
+  };
 
   for (;;) {
+    if (fast) {
+      do {  // two steps per bounds check: each step hands out at most 32 IDs
+        fast_step();
+        fast_step();
+      } while (hoff + 64 <= cur_len);
+    }
+    // General step: lanes may be idle, the tile may run out, tiles change here.
     if (busy) {
-      r = hash_pos<RT>(lseed, r);
+      r = hash_pre<RT>(lspre, r);
       if (chain_stops<RT, HasSeed>(r, l2m0)) {
         stage[sidx] = r;
         busy = false;
       }
     }
     const uint32_t fm = __ballot_sync(kFull, !busy);
-    if (fm == 0) continue;
     const uint32_t nfree = __popc(fm);
     const uint32_t rank = __popc(fm & lt);
     uint32_t taken = 0;
@@ -175,13 +234,10 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
         const uint32_t k = min(avail, nfree - taken);
         if (!busy && rank - taken < k) {
           const uint32_t o = hoff + (rank - taken);
-          const uint64_t i = cur_base + o;
-          sidx = (static_cast<uint32_t>(cur) << shift) + o;
-          r = static_cast<RT>(2 * i + 1);
-          if constexpr (Batched) {
-            lseed = sg[cur].seed;
-            l2m0 = seed_limit<RT>(sg[cur].two_m0);
-          }
+          sidx = cur_s0 + o;
+          r = cur_r0 + 2 * static_cast<RT>(o);
+          lspre = cur_spre;
+          l2m0 = cur_2m0;
           busy = true;
         }
         hoff += k;
@@ -210,8 +266,16 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
       cur_base = nb;
       cur_len = nl;
       hoff = 0;
+      cur_r0 = static_cast<RT>(2 * cur_base + 1);
+      cur_s0 = static_cast<uint32_t>(cur) << shift;
+      if constexpr (Batched) {
+        cur_spre = sg[cur].seed_pre;
+        cur_2m0 = seed_limit<RT>(sg[cur].two_m0);
+      }
     }
-    if (!tiles_left && __ballot_sync(kFull, busy) == 0) break;
+    const uint32_t idle = __ballot_sync(kFull, !busy);
+    if (!tiles_left && idle == kFull) break;
+    fast = idle == 0 && hoff + 64 <= cur_len;
   }
   if (oth_live) flush(oth, oth_base, oth_len);
   flush(cur, cur_base, cur_len);
@@ -281,29 +345,32 @@ __global__ void k_degree_simple(const GraphDev g, uint64_t hit_pos, uint64_t nod
 }
 
 // Adds one end point at node v for every lane with hit set.  Nodes below `hot` go to the
-// CTA's shared-memory bins, one atomic per distinct node per warp; a bin that reaches
-// 2^31 hands 2^31 over to the global counter, so a 32-bit bin never overflows.
-__device__ __forceinline__ void histogram_add(bool hit, uint64_t v, uint32_t *bins, uint32_t hot,
-                                              uint64_t *__restrict__ counts) {
+// CTA's 64-bit shared-memory bins, one atomic per distinct node per warp
+// (__match_any_sync); the rest go to the global counters.  The atomics return nothing, so
+// the warp does not wait for them.
+__device__ __forceinline__ void histogram_add(bool hit, uint64_t v, unsigned long long *bins,
+                                              uint32_t hot, uint64_t *__restrict__ counts) {
   const bool hot_hit = hit && v < hot;
   if (hit && !hot_hit) atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
   const uint32_t key = hot_hit ? static_cast<uint32_t>(v) : 0xffffffffu;
   const uint32_t peers = __match_any_sync(kFull, key);
-  if (hot_hit && (threadIdx.x & 31) == __ffs(peers) - 1) {
-    const uint32_t c = __popc(peers);
-    const uint32_t old = atomicAdd(bins + v, c);
-    if (old < 0x80000000u && old + c >= 0x80000000u) {
-      atomicSub(bins + v, 0x80000000u);
-      atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 0x80000000ull);
-    }
-  }
+  if (hot_hit && (threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicAdd(bins + v, static_cast<unsigned long long>(__popc(peers)));
+}
+
+// One end point at node v from the calling lane alone: a shared-memory bin below `hot`,
+// else the global counter.
+__device__ __forceinline__ void histogram_add_lane(uint64_t v, unsigned long long *bins, uint32_t hot,
+                                                   uint64_t *__restrict__ counts) {
+  if (v < hot) atomicAdd(bins + v, 1ull);
+  else atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
 }
 
 template <class RT, bool HasSeed>
 __global__ void __launch_bounds__(1024)
 k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64_t node_limit,
                 uint32_t hot, uint64_t *__restrict__ counts) {
-  extern __shared__ __align__(16) uint32_t bins[];
+  extern __shared__ __align__(16) unsigned long long bins[];
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) bins[b] = 0;
   __syncthreads();
 
@@ -327,22 +394,50 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       tiles_left = false;
     }
   }
-  bool busy = false;
+  const uint64_t spre = g.seed_pre;
+  const bool agg = sp.hist_agg != 0;
+  RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
+  bool busy = false, fast = false;
   RT r = 0;
-  while (tiles_left || __any_sync(kFull, busy)) {
-    bool hit = false;
-    uint64_t v = 0;
-    if (busy) {
-      r = hash_pos<RT>(g.seed, r);
-      if (chain_stops<RT, HasSeed>(r, two_m0)) {
-        busy = false;
-        if (static_cast<uint64_t>(r) < hit_pos) {
-          v = target_of<RT, HasSeed>(r, g);
-          hit = v < node_limit;
-        }
+
+  // Counts the target of every lane whose chain stopped at r below hit_pos (only those can
+  // name a node below node_limit).  Warp-collective.
+  auto count_hits = [&](bool stop) {
+    bool hit = stop && static_cast<uint64_t>(r) < hit_pos;
+    if (__any_sync(kFull, hit)) {
+      uint64_t v = 0;
+      if (hit) {
+        v = target_of<RT, HasSeed>(r, g);
+        hit = v < node_limit;
       }
+      if (agg) histogram_add(hit, v, bins, hot, counts);
+      else if (hit) histogram_add_lane(v, bins, hot, counts);
     }
-    if (__any_sync(kFull, hit)) histogram_add(hit, v, bins, hot, counts);
+  };
+  // Fast step: every lane busy, >= 32 IDs left in the tile.
+  auto fast_step = [&]() {
+    r = hash_pre<RT>(spre, r);
+    const bool stop = chain_stops<RT, HasSeed>(r, two_m0);
+    count_hits(stop);
+    const uint32_t fm = __ballot_sync(kFull, stop);
+    if (stop) r = cur_r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
+    hoff += __popc(fm);
+  };
+
+  for (;;) {
+    if (fast) {
+      do {  // two steps per bounds check
+        fast_step();
+        fast_step();
+      } while (hoff + 64 <= cur_len);
+    }
+    bool stop = false;
+    if (busy) {
+      r = hash_pre<RT>(spre, r);
+      stop = chain_stops<RT, HasSeed>(r, two_m0);
+    }
+    count_hits(stop);
+    if (stop) busy = false;
     const uint32_t fm = __ballot_sync(kFull, !busy);
     const uint32_t nfree = __popc(fm);
     const uint32_t rank = __popc(fm & lt);
@@ -352,7 +447,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       if (avail > 0) {
         const uint32_t k = min(avail, nfree - taken);
         if (!busy && rank - taken < k) {
-          r = static_cast<RT>(2 * (cur_base + hoff + (rank - taken)) + 1);
+          r = cur_r0 + 2 * static_cast<RT>(hoff + (rank - taken));
           busy = true;
         }
         hoff += k;
@@ -366,12 +461,16 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       }
       cur_base = g.begin + (t << shift);
       cur_len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - cur_base));
+      cur_r0 = static_cast<RT>(2 * cur_base + 1);
       hoff = 0;
     }
+    const uint32_t idle = __ballot_sync(kFull, !busy);
+    if (!tiles_left && idle == kFull) break;
+    fast = idle == 0 && hoff + 64 <= cur_len;
   }
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
-    const uint32_t c = bins[b];
+    const unsigned long long c = bins[b];
     if (c) atomicAdd(reinterpret_cast<unsigned long long *>(counts + b), static_cast<unsigned long long>(c));
   }
 }
@@ -440,6 +539,7 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
   sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
   sp.counter = counter;
   sp.tile_shift = shift;
+  sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
   int grid = 0;
   st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
   if (st != BA_OK) return st;
@@ -467,7 +567,7 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
-  const size_t smem = static_cast<size_t>(hot) * sizeof(uint32_t);
+  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long);
   auto kernel = k_degree_refill<RT, HasSeed>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
@@ -475,6 +575,7 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
   sp.counter = counter;
   sp.tile_shift = shift;
+  sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
   int grid = 0;
   st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
   if (st != BA_OK) return st;
@@ -500,6 +601,7 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
   sp.num_tiles = total_tiles;
   sp.counter = counter;
   sp.tile_shift = shift;
+  sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
   int grid = 0;
   st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (total_tiles + warps - 1) / warps, &grid);
   if (st != BA_OK) return st;

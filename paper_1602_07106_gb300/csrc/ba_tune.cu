@@ -36,7 +36,7 @@ Shape default_shape(int kind) {
   Shape s;
   switch (kind) {
     case BA_KIND_DEGREE:
-      s.block = 512; s.ctas_per_sm = 2; s.tile = 512; s.refill = 1; s.hist_bins = 24576;
+      s.block = 512; s.ctas_per_sm = 2; s.tile = 512; s.refill = 1; s.hist_bins = 12288;
       break;
     default:  // generate and batch
       s.block = 256; s.ctas_per_sm = 4; s.tile = 512; s.refill = 1; s.hist_bins = 0;
@@ -52,6 +52,7 @@ Shape from_public(const ba_tuning &t, int kind) {
   if (t.tile > 0) s.tile = t.tile;
   s.refill = t.refill;
   if (t.hist_bins > 0) s.hist_bins = t.hist_bins;
+  s.hist_agg = t.hist_agg;
   return s;
 }
 
@@ -62,6 +63,7 @@ void to_public(const Shape &s, ba_tuning *t) {
   t->tile = s.tile;
   t->refill = s.refill;
   t->hist_bins = s.hist_bins;
+  t->hist_agg = s.hist_agg;
 }
 
 bool valid_shape(const Shape &s, int kind) {
@@ -71,7 +73,8 @@ bool valid_shape(const Shape &s, int kind) {
   if (s.refill == 1 || kind == BA_KIND_BATCH) {
     if (s.tile < 64 || s.tile > 4096 || (s.tile & (s.tile - 1)) != 0) return false;
   }
-  if (s.hist_bins < 0 || s.hist_bins > 56 * 1024) return false;
+  if (s.hist_bins < 0 || s.hist_bins > 28 * 1024) return false;
+  if (s.hist_agg != 0 && s.hist_agg != 1) return false;
   return true;
 }
 
@@ -95,8 +98,9 @@ ba_status load_file(const char *path, Cache &c) {
     Shape s;
     if (std::sscanf(text.c_str() + pos,
                     "{\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-                    "\"refill\": %d, \"hist_bins\": %d}",
-                    &kind, &r32, &s.block, &s.ctas_per_sm, &s.tile, &s.refill, &s.hist_bins) == 7 &&
+                    "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d}",
+                    &kind, &r32, &s.block, &s.ctas_per_sm, &s.tile, &s.refill, &s.hist_bins,
+                    &s.hist_agg) == 8 &&
         kind >= 0 && kind < kKinds && (r32 == 0 || r32 == 1) && valid_shape(s, kind)) {
       c.tuned[kind][r32] = s;
       c.has_tuned[kind][r32] = true;
@@ -141,7 +145,7 @@ ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out) {
   Shape s = from_public(*t, kind);
   if (!valid_shape(s, kind)) {
     set_error("invalid launch shape (block multiple of 32 <= 1024, tile power of two 64..4096, "
-              "refill 0 or 1, hist_bins <= 57344)");
+              "refill 0 or 1, hist_bins <= 28672, hist_agg 0 or 1)");
     return BA_ERR_INVALID_ARG;
   }
   *out = s;
@@ -193,15 +197,18 @@ std::vector<Shape> candidates(int kind) {
   const int tiles[] = {256, 512, 1024};
   if (kind == BA_KIND_DEGREE) {
     const int dblocks[] = {256, 512, 1024};
-    const int bins[] = {8192, 16384, 24576, 49152};
+    const int bins[] = {4096, 8192, 12288, 24576};
     for (int blk : dblocks)
       for (int ctas : {1, 2, 4})
         for (int tile : tiles)
           for (int hb : bins) {
-            if (blk * ctas > 2048 || static_cast<size_t>(hb) * 4 * ctas > 220 * 1024) continue;
-            Shape s;
-            s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1; s.hist_bins = hb;
-            out.push_back(s);
+            if (blk * ctas > 2048 || static_cast<size_t>(hb) * 8 * ctas > 220 * 1024) continue;
+            for (int agg : {0, 1}) {
+              Shape s;
+              s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1; s.hist_bins = hb;
+              s.hist_agg = agg;
+              out.push_back(s);
+            }
           }
     Shape simple;
     simple.block = 256; simple.ctas_per_sm = 8; simple.tile = 512; simple.refill = 0;
@@ -375,8 +382,9 @@ ba_status ba_tune_save(const char *path) {
       const Shape &s = c.tuned[k][r];
       std::fprintf(f,
                    "%s\n  {\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-                   "\"refill\": %d, \"hist_bins\": %d}",
-                   firstw ? "" : ",", k, r, s.block, s.ctas_per_sm, s.tile, s.refill, s.hist_bins);
+                   "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d}",
+                   firstw ? "" : ",", k, r, s.block, s.ctas_per_sm, s.tile, s.refill, s.hist_bins,
+                   s.hist_agg);
       firstw = false;
     }
   std::fprintf(f, "\n]}\n");

@@ -76,7 +76,7 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
     default = ba.ba_get_tuning(ba.BA_KIND_GENERATE)
     assert default["block"] % 32 == 0 and default["tile"] & (default["tile"] - 1) == 0
     for bad in ({"block": 100, "refill": 1}, {"tile": 100, "refill": 1}, {"refill": 3},
-                {"block": 2048, "refill": 1}):
+                {"block": 2048, "refill": 1}, {"refill": 1, "hist_agg": 2}):
         with pytest.raises(ba.BAError):
             ba.ba_set_tuning(ba.BA_KIND_GENERATE, bad)
     ba.ba_set_tuning(ba.BA_KIND_GENERATE, {"block": 128, "ctas_per_sm": 8, "tile": 1024,
@@ -86,9 +86,10 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
     assert ba.ba_get_tuning(ba.BA_KIND_GENERATE) == default
     path = tmp_path / "tune.json"
     path.write_text('{"sm_count": 152, "entries": [\n  {"kind": 1, "r32": 0, "block": 256, '
-                    '"ctas_per_sm": 4, "tile": 256, "refill": 1, "hist_bins": 8192}\n]}\n')
+                    '"ctas_per_sm": 4, "tile": 256, "refill": 1, "hist_bins": 8192, "hist_agg": 1}\n]}\n')
     ba.ba_tune_load(str(path))
     assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["hist_bins"] == 8192
+    assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["hist_agg"] == 1
     out = tmp_path / "saved.json"
     ba.ba_tune_save(str(out))
     assert '"hist_bins": 8192' in out.read_text()
