@@ -145,14 +145,16 @@ ba_status ba_set_tuning(int32_t kind, const ba_tuning *tune);
 ba_status ba_get_tuning(int32_t kind, uint64_t edge_end, ba_tuning *out);
 
 /*
- * Autotuner: times candidate shapes (block size, CTAs/SM, tile, refill, histogram
- * bins) for `kind` on the sample graph (seed, n, d, n0) range [0, edge_end) -- for
- * BA_KIND_GENERATE it needs scratch_dev of 2*edge_end int64 -- keeps the fastest in the
- * in-process cache (keyed by kind and 32/64-bit position path) and writes it to
+ * Autotuner: times candidate shapes (block size, CTAs/SM, tile, refill, histogram bins and
+ * aggregation) for `kind` on the sample range [edge_begin, edge_end) of the graph
+ * (seed, n, d, n0) -- for BA_KIND_GENERATE and BA_KIND_BATCH it needs scratch_dev of
+ * 2*(edge_end-edge_begin) int64 -- keeps the fastest in the in-process cache (keyed by
+ * kind and 32/64-bit position path, the path being that of edge_end) and writes it to
  * out (may be NULL).  Synchronises `stream`.
  */
 ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
-                  uint64_t edge_end, int64_t *scratch_dev, void *stream, ba_tuning *out);
+                  uint64_t edge_begin, uint64_t edge_end, int64_t *scratch_dev, void *stream,
+                  ba_tuning *out);
 
 /* Save / load the tuner cache as JSON text (path NULL = $BA_TUNE_CACHE).  The cache is
  * loaded automatically from $BA_TUNE_CACHE at the first call when that variable is set. */

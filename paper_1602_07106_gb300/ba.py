@@ -75,7 +75,7 @@ _sig("ba_degree_count_range", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, 
      ctypes.c_int, _vp)
 _sig("ba_set_tuning", ctypes.c_int, _i32, ctypes.POINTER(ba_tuning))
 _sig("ba_get_tuning", ctypes.c_int, _i32, _u64, ctypes.POINTER(ba_tuning))
-_sig("ba_tune", ctypes.c_int, _i32, _u64, _u64, _u32, _u64, _u64, _vp, _vp,
+_sig("ba_tune", ctypes.c_int, _i32, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _vp,
      ctypes.POINTER(ba_tuning))
 _sig("ba_tune_save", ctypes.c_int, ctypes.c_char_p)
 _sig("ba_tune_load", ctypes.c_int, ctypes.c_char_p)
@@ -203,10 +203,10 @@ def ba_get_tuning(kind: int, edge_end: int = 1) -> dict:
     return t.as_dict()
 
 
-def ba_tune(kind, seed, n, d, n0, edge_end, scratch=None, stream=None) -> dict:
+def ba_tune(kind, seed, n, d, n0, edge_begin, edge_end, scratch=None, stream=None) -> dict:
     t = ba_tuning()
-    _check(_lib.ba_tune(kind, seed, n, d, n0, edge_end, _ptr(scratch), _stream(stream),
-                        ctypes.byref(t)), "ba_tune")
+    _check(_lib.ba_tune(kind, seed, n, d, n0, edge_begin, edge_end, _ptr(scratch),
+                        _stream(stream), ctypes.byref(t)), "ba_tune")
     return t.as_dict()
 
 

@@ -109,10 +109,13 @@ __device__ __forceinline__ uint32_t div32(uint32_t x, const FastDiv &f) {
 
 // Seed clique (section 4): position p < 2 m0 belongs to seed edge k = p/2 = v(v-1)/2 + u,
 // E[2k] = v, E[2k+1] = u.  v comes from the quadratic formula, corrected to the exact
-// integer (the estimate is off by at most one).  Rare on the hot path.
+// integer by the two loops.  The estimate uses single precision (fast on every SM; off by
+// at most a few steps below 2^40) and double precision only for larger seed cliques.
 __device__ __forceinline__ uint64_t clique_position(uint64_t p) {
   const uint64_t k = p >> 1;
-  uint64_t v = static_cast<uint64_t>((1.0 + sqrt(8.0 * static_cast<double>(k) + 1.0)) * 0.5);
+  uint64_t v = k < (1ull << 40)
+                   ? static_cast<uint64_t>((1.0f + sqrtf(8.0f * static_cast<float>(k) + 1.0f)) * 0.5f)
+                   : static_cast<uint64_t>((1.0 + sqrt(8.0 * static_cast<double>(k) + 1.0)) * 0.5);
   while (v > 1 && v * (v - 1) / 2 > k) --v;
   while (v * (v + 1) / 2 <= k) ++v;
   return (p & 1) ? k - v * (v - 1) / 2 : v;

@@ -91,6 +91,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     const uint32_t m0 = static_cast<uint32_t>(g.m0);
     const uint32_t b32 = static_cast<uint32_t>(base);
     int4 *dst = reinterpret_cast<int4 *>(out) + out0;
+#pragma unroll 4
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
       const uint32_t i = b32 + j;
       uint32_t u, v;
@@ -396,22 +397,38 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   }
   const uint64_t spre = g.seed_pre;
   const bool agg = sp.hist_agg != 0;
+  // Only a chain that stops below hit_pos can name a node below node_limit.  As a 32-bit
+  // position, hit_pos >= 2^32 saturates (every stopped 32-bit position is below it).
+  const RT hp = (sizeof(RT) == 4 && hit_pos > 0xffffffffull) ? static_cast<RT>(0xffffffffu)
+                                                             : static_cast<RT>(hit_pos);
   RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
   bool busy = false, fast = false;
   RT r = 0;
 
-  // Counts the target of every lane whose chain stopped at r below hit_pos (only those can
-  // name a node below node_limit).  Warp-collective.
+  // Stopped positions below hp wait in a per-warp ring of 64; once 32 have gathered the
+  // whole warp resolves them together (one target per lane) and counts them.
+  RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * 64;
+  uint32_t qhead = 0, qtail = 0;  // warp-uniform
+  auto drain = [&](uint32_t k) {  // ring entries qhead .. qhead+k-1, k <= 32
+    __syncwarp();
+    bool hit = static_cast<uint32_t>(lane) < k;
+    uint64_t v = 0;
+    if (hit) {
+      v = target_of<RT, HasSeed>(ring[(qhead + lane) & 63], g);
+      hit = v < node_limit;
+    }
+    if (agg) histogram_add(hit, v, bins, hot, counts);
+    else if (hit) histogram_add_lane(v, bins, hot, counts);
+    qhead += k;
+    __syncwarp();
+  };
   auto count_hits = [&](bool stop) {
-    bool hit = stop && static_cast<uint64_t>(r) < hit_pos;
-    if (__any_sync(kFull, hit)) {
-      uint64_t v = 0;
-      if (hit) {
-        v = target_of<RT, HasSeed>(r, g);
-        hit = v < node_limit;
-      }
-      if (agg) histogram_add(hit, v, bins, hot, counts);
-      else if (hit) histogram_add_lane(v, bins, hot, counts);
+    const bool hit = stop && r < hp;
+    const uint32_t hm = __ballot_sync(kFull, hit);
+    if (hm) {
+      if (hit) ring[(qtail + __popc(hm & lt)) & 63] = r;
+      qtail += __popc(hm);
+      if (qtail - qhead >= 32) drain(32);
     }
   };
   // Fast step: every lane busy, >= 32 IDs left in the tile.
@@ -468,6 +485,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     if (!tiles_left && idle == kFull) break;
     fast = idle == 0 && hoff + 64 <= cur_len;
   }
+  if (qtail != qhead) drain(qtail - qhead);
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
     const unsigned long long c = bins[b];
@@ -567,7 +585,8 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
-  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long);
+  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
+                      static_cast<size_t>(warps) * 64 * sizeof(RT);  // bins + hit rings
   auto kernel = k_degree_refill<RT, HasSeed>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;

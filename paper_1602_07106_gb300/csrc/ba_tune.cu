@@ -36,7 +36,7 @@ Shape default_shape(int kind) {
   Shape s;
   switch (kind) {
     case BA_KIND_DEGREE:
-      s.block = 512; s.ctas_per_sm = 2; s.tile = 512; s.refill = 1; s.hist_bins = 12288;
+      s.block = 512; s.ctas_per_sm = 2; s.tile = 2048; s.refill = 1; s.hist_bins = 12288;
       break;
     default:  // generate and batch
       s.block = 256; s.ctas_per_sm = 4; s.tile = 512; s.refill = 1; s.hist_bins = 0;
@@ -264,7 +264,8 @@ ba_status ba_get_tuning(int32_t kind, uint64_t edge_end, ba_tuning *out) {
 }
 
 ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
-                  uint64_t edge_end, int64_t *scratch_dev, void *stream, ba_tuning *out) {
+                  uint64_t edge_begin, uint64_t edge_end, int64_t *scratch_dev, void *stream,
+                  ba_tuning *out) {
   set_error("");
   if (kind < 0 || kind >= kKinds) {
     set_error("unknown kernel kind");
@@ -273,12 +274,13 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
   uint64_t m = 0;
   ba_status st = validate_graph(n, d, n0, &m);
   if (st != BA_OK) return st;
-  if (edge_end == 0 || edge_end > m) {
-    set_error("tuning range must be 1..m edges");
+  if (edge_begin >= edge_end || edge_end > m) {
+    set_error("tuning range must be a non-empty range inside 0..m");
     return BA_ERR_RANGE;
   }
+  const uint64_t len = edge_end - edge_begin;
   if (kind != BA_KIND_DEGREE && (scratch_dev == nullptr || (reinterpret_cast<uintptr_t>(scratch_dev) & 15))) {
-    set_error("generate/batch tuning needs a 16-byte aligned scratch of 2*edge_end int64");
+    set_error("generate/batch tuning needs a 16-byte aligned scratch of 2*(edge_end-edge_begin) int64");
     return BA_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -298,10 +300,10 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
   const int kSlices = 64;
   std::vector<GraphDev> graphs;
   if (kind == BA_KIND_BATCH) {
-    const uint64_t step = (edge_end + kSlices - 1) / kSlices;
-    for (uint64_t a = 0; a < edge_end; a += step) {
+    const uint64_t step = (len + kSlices - 1) / kSlices;
+    for (uint64_t a = edge_begin; a < edge_end; a += step) {
       GraphDev g = make_graph_dev(seed, n, d, n0, a, std::min(edge_end, a + step));
-      g.out_edge = a;
+      g.out_edge = a - edge_begin;
       graphs.push_back(g);
     }
     e = cudaMallocAsync(&tab_mem, graphs.size() * sizeof(GraphDev) + (graphs.size() + 1) * 8, s);
@@ -310,7 +312,7 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
       return cuda_fail(e, "cudaMallocAsync");
     }
   }
-  const GraphDev g = make_graph_dev(seed, n, d, n0, 0, edge_end);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
   float best_ms = 1e30f;
   Shape best = default_shape(kind);
   for (const Shape &cand : candidates(kind)) {

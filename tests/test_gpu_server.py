@@ -93,12 +93,12 @@ def test_autotuner_picks_a_valid_shape_and_output_is_unchanged(ba):
     m = n * d
     scratch = torch.empty((m, 2), dtype=torch.int64, device="cuda")
     before = _plain(ba, 3, n, d, 0, 0, m).clone()
-    shape = ba.ba_tune(ba.BA_KIND_GENERATE, 3, n, d, 0, m, scratch)
+    shape = ba.ba_tune(ba.BA_KIND_GENERATE, 3, n, d, 0, 0, m, scratch)
     assert shape["block"] % 32 == 0
     assert ba.ba_get_tuning(ba.BA_KIND_GENERATE, m) == shape
     assert torch.equal(_plain(ba, 3, n, d, 0, 0, m), before)
-    dshape = ba.ba_tune(ba.BA_KIND_DEGREE, 3, n, d, 0, m)
+    dshape = ba.ba_tune(ba.BA_KIND_DEGREE, 3, n, d, 0, m // 2, m)
     assert dshape["block"] % 32 == 0
-    bshape = ba.ba_tune(ba.BA_KIND_BATCH, 3, n, d, 0, m, scratch)
+    bshape = ba.ba_tune(ba.BA_KIND_BATCH, 3, n, d, 0, 0, m, scratch)
     assert bshape["block"] % 32 == 0
     assert torch.equal(_plain(ba, 3, n, d, 0, 0, m), before)
