@@ -94,6 +94,7 @@ GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint
   g.div.l = l;
   g.div.m64 = static_cast<uint64_t>(((one << (62 + l)) + d - 1) / d);
   g.div.m32 = static_cast<uint32_t>(((one << (31 + l)) + d - 1) / d);
+  g.div.pow2 = (d & (d - 1)) == 0 ? 1u : 0u;
   return g;
 }
 

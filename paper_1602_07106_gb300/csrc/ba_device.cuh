@@ -97,7 +97,8 @@ struct FastDiv {
   uint64_t m64;
   uint32_t l;
   uint32_t m32;
-  uint32_t pad[2];
+  uint32_t pow2;  // d == 2^l
+  uint32_t pad;
 };
 
 __device__ __forceinline__ uint64_t div64(uint64_t x, const FastDiv &f) {

@@ -19,6 +19,7 @@
 //                      shared-memory limit go to a per-CTA histogram with warp-aggregated
 //                      atomics (__match_any_sync), the rest to global 64-bit atomics.
 #include <algorithm>
+#include <type_traits>
 
 #include "ba_internal.h"
 
@@ -91,21 +92,31 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     const uint32_t m0 = static_cast<uint32_t>(g.m0);
     const uint32_t b32 = static_cast<uint32_t>(base);
     int4 *dst = reinterpret_cast<int4 *>(out) + out0;
+    // d a power of two (d = 2^l): the divisions are shifts.
+    auto body = [&](auto pow2_tag) {
+      constexpr bool Pow2 = decltype(pow2_tag)::value;
+      auto div = [&](uint32_t x) -> uint32_t {
+        if constexpr (Pow2) return x >> g.div.l;
+        else return div32(x, g.div);
+      };
 #pragma unroll 4
-    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
-      const uint32_t i = b32 + j;
-      uint32_t u, v;
-      if (HasSeed && i < g.m0) {
-        u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
-        v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
-      } else {
-        const uint32_t r = stage[j];
-        u = n0 + div32(i - m0, g.div);
-        v = (HasSeed && r < g.two_m0) ? static_cast<uint32_t>(clique_position(r))
-                                      : n0 + div32((r >> 1) - m0, g.div);
+      for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+        const uint32_t i = b32 + j;
+        uint32_t u, v;
+        if (HasSeed && i < g.m0) {
+          u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
+          v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
+        } else {
+          const uint32_t r = stage[j];
+          u = n0 + div(i - m0);
+          v = (HasSeed && r < g.two_m0) ? static_cast<uint32_t>(clique_position(r))
+                                        : n0 + div((r >> 1) - m0);
+        }
+        __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       }
-      __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
-    }
+    };
+    if (g.div.pow2) body(std::true_type{});
+    else body(std::false_type{});
   } else {
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
       const uint64_t i = base + j;
@@ -145,11 +156,12 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   bool first = true;
 
   // Loads tile t into slot `slot`; false when the launch has no tile t.
-  auto fetch = [&](int slot, uint64_t &base, uint32_t &len) -> bool {
+  auto fetch = [&](int slot, uint64_t &base, uint32_t &len, int &gi) -> bool {
     const uint64_t t = next_tile(sp, first, gwarp);
     if (t >= sp.num_tiles) return false;
+    gi = 0;
     if constexpr (Batched) {
-      const int gi = graph_of_tile(tab, t);
+      gi = graph_of_tile(tab, t);
       copy_graph(sg + slot, tab.graphs + gi);
       base = sg[slot].begin + ((t - sg[slot].tile0) << shift);
       len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), sg[slot].end - base));
@@ -171,13 +183,14 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   uint64_t cur_base = 0, oth_base = 0;
   uint32_t cur_len = 0, oth_len = 0, hoff = 0;
   bool oth_live = false, tiles_left = true;
-  if (!fetch(cur, cur_base, cur_len)) return;
+  int cur_gi = 0, oth_gi = 0;
+  if (!fetch(cur, cur_base, cur_len, cur_gi)) return;
   // What a lane needs to start edge cur_base + o: position r = cur_r0 + 2o, stage slot
   // cur_s0 + o, and (batched) the seed and seed size of the tile's graph.
   RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
   uint32_t cur_s0 = static_cast<uint32_t>(cur) << shift;
   uint64_t cur_spre = g0.seed_pre;
-  RT cur_2m0 = seed_limit<RT>(g0.two_m0);
+  RT cur_2m0 = seed_limit<RT>(g0.two_m0), oth_2m0 = 0;
   if constexpr (Batched) {
     cur_spre = sg[cur].seed_pre;
     cur_2m0 = seed_limit<RT>(sg[cur].two_m0);
@@ -191,31 +204,52 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   RT l2m0 = cur_2m0;
   bool fast = false;
 
-  // Fast step: every lane is busy and the current tile still has >= 32 IDs to hand out,
-  // so each lane whose chain stops parks r and starts the next ID at once.
-  auto fast_step = [&]() {
-    r = hash_pre<RT>(lspre, r);
-    const bool stop = chain_stops<RT, HasSeed>(r, l2m0);
-    if (stop) stage[sidx] = r;
-    const uint32_t fm = __ballot_sync(kFull, stop);
-    if (stop) {
-      const uint32_t o = hoff + __popc(fm & lt);
-      sidx = cur_s0 + o;
-      r = cur_r0 + 2 * static_cast<RT>(o);
-      if constexpr (Batched) {
-        lspre = cur_spre;
-        l2m0 = cur_2m0;
+  // Fast steps: every lane is busy and the current tile still has >= 64 IDs to hand out,
+  // so each lane whose chain stops parks r and starts the next ID at once.  Seed: a tile
+  // in flight belongs to a graph with a seed clique; Assign: the two tiles in flight belong
+  // to different graphs, so a lane takes the current graph's constants with its new ID.
+  auto fast_loop = [&](auto seed_tag, auto assign_tag) {
+    constexpr bool Seed = decltype(seed_tag)::value;
+    constexpr bool Assign = decltype(assign_tag)::value;
+    auto step = [&]() {
+      r = hash_pre<RT>(lspre, r);
+      const bool stop = chain_stops<RT, Seed>(r, l2m0);
+      if (stop) stage[sidx] = r;
+      const uint32_t fm = __ballot_sync(kFull, stop);
+      if (stop) {
+        const uint32_t o = hoff + __popc(fm & lt);
+        sidx = cur_s0 + o;
+        r = cur_r0 + 2 * static_cast<RT>(o);
+        if constexpr (Assign) {
+          lspre = cur_spre;
+          l2m0 = cur_2m0;
+        }
       }
-    }
-    hoff += __popc(fm);
+      hoff += __popc(fm);
+    };
+    do {  // two steps per bounds check: each step hands out at most 32 IDs
+      step();
+      step();
+    } while (hoff + 64 <= cur_len);
   };
 
   for (;;) {
     if (fast) {
-      do {  // two steps per bounds check: each step hands out at most 32 IDs
-        fast_step();
-        fast_step();
-      } while (hoff + 64 <= cur_len);
+      const bool mixed = Batched && oth_live && oth_gi != cur_gi;
+      if constexpr (HasSeed) {
+        if (cur_2m0 != 0 || (oth_live && oth_2m0 != 0)) {
+          if (mixed) fast_loop(std::true_type{}, std::true_type{});
+          else fast_loop(std::true_type{}, std::false_type{});
+        } else if (mixed) {
+          fast_loop(std::false_type{}, std::true_type{});
+        } else {
+          fast_loop(std::false_type{}, std::false_type{});
+        }
+      } else if (mixed) {
+        fast_loop(std::false_type{}, std::true_type{});
+      } else {
+        fast_loop(std::false_type{}, std::false_type{});
+      }
     }
     // General step: lanes may be idle, the tile may run out, tiles change here.
     if (busy) {
@@ -254,18 +288,22 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
       }
       uint64_t nb;
       uint32_t nl;
-      if (!fetch(oth, nb, nl)) {
+      int ngi;
+      if (!fetch(oth, nb, nl, ngi)) {
         tiles_left = false;
         break;
       }
       oth_base = cur_base;
       oth_len = cur_len;
+      oth_gi = cur_gi;
+      oth_2m0 = cur_2m0;
       oth_live = true;
       const int tmp = cur;
       cur = oth;
       oth = tmp;
       cur_base = nb;
       cur_len = nl;
+      cur_gi = ngi;
       hoff = 0;
       cur_r0 = static_cast<RT>(2 * cur_base + 1);
       cur_s0 = static_cast<uint32_t>(cur) << shift;
