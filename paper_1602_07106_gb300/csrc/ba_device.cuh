@@ -113,6 +113,13 @@ __device__ __forceinline__ uint32_t div32(uint32_t x, const FastDiv &f) {
 // integer by the two loops.  The estimate uses single precision (fast on every SM; off by
 // at most a few steps below 2^40) and double precision only for larger seed cliques.
 __device__ __forceinline__ uint64_t clique_position(uint64_t p) {
+  if (p < (1ull << 31)) {  // 32-bit fast path: k < 2^30, so v <= 46341 and v(v+1) < 2^32
+    const uint32_t k = static_cast<uint32_t>(p >> 1);
+    uint32_t v = static_cast<uint32_t>((1.0f + sqrtf(8.0f * static_cast<float>(k) + 1.0f)) * 0.5f);
+    while (v > 1 && v * (v - 1) / 2 > k) --v;
+    while (v * (v + 1) / 2 <= k) ++v;
+    return (p & 1) ? k - v * (v - 1) / 2 : v;
+  }
   const uint64_t k = p >> 1;
   uint64_t v = k < (1ull << 40)
                    ? static_cast<uint64_t>((1.0f + sqrtf(8.0f * static_cast<float>(k) + 1.0f)) * 0.5f)

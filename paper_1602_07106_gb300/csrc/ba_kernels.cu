@@ -102,15 +102,21 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 #pragma unroll 4
       for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
         const uint32_t i = b32 + j;
-        uint32_t u, v;
-        if (HasSeed && i < g.m0) {
-          u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
-          v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
-        } else {
-          const uint32_t r = stage[j];
-          u = n0 + div(i - m0);
-          v = (HasSeed && r < g.two_m0) ? static_cast<uint32_t>(clique_position(r))
-                                        : n0 + div((r >> 1) - m0);
+        const uint32_t r = stage[j];
+        uint32_t u = n0 + div(i - m0);
+        uint32_t v = n0 + div((r >> 1) - m0);
+        if constexpr (HasSeed) {
+          // Seed edges and chains that stopped inside the seed are rare: look them up
+          // behind a warp vote so the common case never pays for the clique arithmetic.
+          const bool seed_edge = i < g.m0, seed_target = r < g.two_m0;
+          if (__any_sync(__activemask(), seed_edge || seed_target)) {
+            if (seed_edge) {
+              u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
+              v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
+            } else if (seed_target) {
+              v = static_cast<uint32_t>(clique_position(r));
+            }
+          }
         }
         __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       }
