@@ -477,6 +477,20 @@ def extras(args, ba, torch, stream, main):
                                             "nodes < 1e5 (section 3 experiment at 1/1000 scale)",
                                 "edges_per_s": g.m / min(ts), "seconds": min(ts),
                                 "degree_sum_first_1e5": int(counts.sum())}
+    # the large workload with 32-bit node IDs (8 bytes per edge)
+    gl = W.PLAIN_LARGE
+    o32 = torch.empty((gl.m, 2), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        ba.ba_generate_edges32(gl.seed, gl.n, gl.d, 0, 0, gl.m, o32, stream)
+    ts = _time_events(lambda: ba.ba_generate_edges32(gl.seed, gl.n, gl.d, 0, 0, gl.m, o32, stream),
+                      stream, torch, 5)
+    t32 = statistics.median(ts)
+    peaks, peak_kind = measured_peaks()
+    ex["plain_large_int32"] = {"workload": "n=2^27 d=16 seed=42, all 2^31 edges as int32 pairs (17.2 GB)",
+                               "edges_per_s": gl.m / t32, "ms": 1e3 * t32,
+                               "hbm_gbs": 8 * gl.m / t32 / 1e9,
+                               "hbm_frac": 8 * gl.m / t32 / 1e9 / float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))}
+    del o32
     # small workload, launch-dominated: median of repeated calls
     s = W.PLAIN_SMALL
     out_s = torch.empty((s.m, 2), dtype=torch.int64, device="cuda")

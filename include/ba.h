@@ -83,6 +83,16 @@ ba_status ba_generate_edges(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
                             int64_t *out_dev, void *stream);
 
 /*
+ * ba_generate_edges with 32-bit node IDs: out_dev holds 2*(edge_end-edge_begin) int32,
+ * 8-byte aligned, edge i at out_dev[2(i-edge_begin)] (source) and [...+1] (target); 8 bytes
+ * per edge instead of 16 (the paper's remark that 32-bit IDs save time for smaller graphs,
+ * section 3).  Needs n <= 2^31 (else BA_ERR_INVALID_ARG); the values equal the int64 call's.
+ */
+ba_status ba_generate_edges32(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                              uint64_t edge_begin, uint64_t edge_end,
+                              int32_t *out_dev, void *stream);
+
+/*
  * Same result as ba_generate_edges, written to HOST memory: host_out holds
  * 2*(edge_end-edge_begin) int64 (pinned memory gives full copy speed; pageable memory
  * works but is slower).  The range is generated in chunks into device staging buffers

@@ -70,6 +70,7 @@ _sig("ba_version", ctypes.c_int)
 _sig("ba_num_edges", _u64, _u64, _u32, _u64)
 _sig("ba_generate_edges", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _vp)
 _sig("ba_generate_edges_host", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _vp)
+_sig("ba_generate_edges32", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _vp)
 _sig("ba_degree_count", ctypes.c_int, _u64, _u64, _u32, _u64, _vp, _vp)
 _sig("ba_degree_count_range", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _u64, _vp,
      ctypes.c_int, _vp)
@@ -158,6 +159,12 @@ def ba_generate_edges(seed, n, d, n0, edge_begin, edge_end, out, stream=None) ->
     _need_cuda(out, torch.int64, 2 * (edge_end - edge_begin), "ba_generate_edges out")
     _check(_lib.ba_generate_edges(seed, n, d, n0, edge_begin, edge_end, _ptr(out),
                                   _stream(stream)), "ba_generate_edges")
+
+
+def ba_generate_edges32(seed, n, d, n0, edge_begin, edge_end, out, stream=None) -> None:
+    _need_cuda(out, torch.int32, 2 * (edge_end - edge_begin), "ba_generate_edges32 out")
+    _check(_lib.ba_generate_edges32(seed, n, d, n0, edge_begin, edge_end, _ptr(out),
+                                    _stream(stream)), "ba_generate_edges32")
 
 
 def ba_generate_edges_host(seed, n, d, n0, edge_begin, edge_end, host_out, stream=None) -> None:

@@ -169,6 +169,34 @@ ba_status ba_generate_edges(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
   return launch_generate(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr), s);
 }
 
+ba_status ba_generate_edges32(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                              uint64_t edge_begin, uint64_t edge_end, int32_t *out_dev,
+                              void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  if (n > (1ull << 31)) {
+    set_error("int32 output needs every node ID below 2^31 (n <= 2^31)");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (edge_begin == edge_end) return BA_OK;
+  if (out_dev == nullptr || (reinterpret_cast<uintptr_t>(out_dev) & 7) != 0) {
+    set_error("out must be a non-NULL, 8-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  const Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  StreamScratch scratch;
+  if (shape.refill != 0) {
+    st = scratch.alloc(sizeof(unsigned long long), s);
+    if (st != BA_OK) return st;
+  }
+  return launch_generate(g, reinterpret_cast<int64_t *>(out_dev), shape,
+                         static_cast<unsigned long long *>(scratch.ptr), s, true);
+}
+
 ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
                                 uint64_t edge_begin, uint64_t edge_end, uint64_t node_limit,
                                 uint64_t *counts_dev, int accumulate, void *stream) {

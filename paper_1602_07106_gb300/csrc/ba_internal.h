@@ -51,8 +51,9 @@ void shape_store(int kind, bool r32, const Shape &s);
 
 // ---- kernel launchers (ba_kernels.cu).  All enqueue on `stream` and return BA_OK or
 // BA_ERR_CUDA.  `counter` must point to >= 8 bytes of device memory; it is zeroed here.
+// narrow: write (source, target) as two int32 (8 bytes per edge) instead of two int64.
 ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
-                          unsigned long long *counter, cudaStream_t stream);
+                          unsigned long long *counter, cudaStream_t stream, bool narrow = false);
 ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                         int accumulate, const Shape &s, unsigned long long *counter,
                         cudaStream_t stream);

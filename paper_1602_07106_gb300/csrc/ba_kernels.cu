@@ -32,14 +32,23 @@ thread_local int g_kernel_count = 0;
 
 // ------------------------------------------------------------------ simple kernels --
 
-template <class RT, bool HasSeed>
+// One (source, target) pair: two int64 (16 bytes) or, with Narrow, two int32 (8 bytes).
+template <bool Narrow>
+__device__ __forceinline__ void store_pair(int64_t *out, uint64_t k, uint64_t u, uint64_t v) {
+  if constexpr (Narrow)
+    __stcs(reinterpret_cast<int2 *>(out) + k, make_int2(static_cast<int>(u), static_cast<int>(v)));
+  else
+    store_edge(out, k, u, v);
+}
+
+template <class RT, bool HasSeed, bool Narrow>
 __global__ void k_generate_simple(const GraphDev g, int64_t *__restrict__ out) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t i = g.begin + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
        i < g.end; i += stride) {
     uint64_t u, v;
     generate_edge<RT, HasSeed>(i, g, u, v);
-    store_edge(out, g.out_edge + (i - g.begin), u, v);
+    store_pair<Narrow>(out, g.out_edge + (i - g.begin), u, v);
   }
 }
 
@@ -79,8 +88,9 @@ __device__ __forceinline__ void copy_graph(GraphDev *dst, const GraphDev *src) {
 }
 
 // Writes the finished tile [base, base+len) of one slot: lane j of the warp handles
-// edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes.
-template <class RT, bool HasSeed>
+// edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes (256 with
+// Narrow int32 pairs).
+template <class RT, bool HasSeed, bool Narrow = false>
 __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint32_t len,
                                            const GraphDev &g, int64_t *__restrict__ out) {
   __syncwarp();
@@ -92,6 +102,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     const uint32_t m0 = static_cast<uint32_t>(g.m0);
     const uint32_t b32 = static_cast<uint32_t>(base);
     int4 *dst = reinterpret_cast<int4 *>(out) + out0;
+    int2 *dst2 = reinterpret_cast<int2 *>(out) + out0;
     // d a power of two (d = 2^l): the divisions are shifts.
     auto body = [&](auto pow2_tag) {
       constexpr bool Pow2 = decltype(pow2_tag)::value;
@@ -118,7 +129,10 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
             }
           }
         }
-        __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
+        if constexpr (Narrow)
+          __stcs(dst2 + j, make_int2(static_cast<int>(u), static_cast<int>(v)));
+        else
+          __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       }
     };
     if (g.div.pow2) body(std::true_type{});
@@ -134,7 +148,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         u = source_of<RT, HasSeed>(i, g);
         v = target_of<RT, HasSeed>(stage[j], g);
       }
-      store_edge(out, out0 + j, u, v);
+      store_pair<Narrow>(out, out0 + j, u, v);
     }
   }
   __syncwarp();
@@ -142,7 +156,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 
 // ----------------------------------------------------------- refill generate kernel --
 
-template <class RT, bool HasSeed, bool Batched>
+template <class RT, bool HasSeed, bool Batched, bool Narrow = false>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
                   int64_t *__restrict__ out) {
@@ -181,7 +195,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     if constexpr (Batched)
       flush_tile<RT, HasSeed>(stage + (slot << shift), base, len, sg[slot], out);
     else
-      flush_tile<RT, HasSeed>(stage + (slot << shift), base, len, g0, out);
+      flush_tile<RT, HasSeed, Narrow>(stage + (slot << shift), base, len, g0, out);
   };
 
   // Warp-uniform slot state: `cur` is the tile being handed out, `oth` the older one.
@@ -577,24 +591,24 @@ ba_status check_launch(const char *what) {
   return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
 }
 
-template <class RT, bool HasSeed>
+template <class RT, bool HasSeed, bool Narrow>
 ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
                      cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
   if (s.refill == 0) {
     int grid = 0;
-    ba_status st = persistent_grid(k_generate_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
+    ba_status st = persistent_grid(k_generate_simple<RT, HasSeed, Narrow>, block, 0, s.ctas_per_sm,
                                    (len + block - 1) / block, &grid);
     if (st != BA_OK) return st;
-    k_generate_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, out);
+    k_generate_simple<RT, HasSeed, Narrow><<<grid, block, 0, stream>>>(g, out);
     g_kernel_count = 1;
     return check_launch("k_generate_simple");
   }
   const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * 2 * (size_t{1} << shift) * sizeof(RT);
-  auto kernel = k_generate_refill<RT, HasSeed, false>;
+  auto kernel = k_generate_refill<RT, HasSeed, false, Narrow>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   SchedParams sp{};
@@ -682,14 +696,20 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
 int last_kernel_count() { return g_kernel_count; }
 
 ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
-                          unsigned long long *counter, cudaStream_t stream) {
+                          unsigned long long *counter, cudaStream_t stream, bool narrow) {
   g_kernel_count = 0;
   const bool r32 = g.end <= (1ull << 31);
   const bool seed = g.m0 > 0;
-  if (r32) return seed ? generate_t<uint32_t, true>(g, out, s, counter, stream)
-                       : generate_t<uint32_t, false>(g, out, s, counter, stream);
-  return seed ? generate_t<uint64_t, true>(g, out, s, counter, stream)
-              : generate_t<uint64_t, false>(g, out, s, counter, stream);
+  if (narrow) {
+    if (r32) return seed ? generate_t<uint32_t, true, true>(g, out, s, counter, stream)
+                         : generate_t<uint32_t, false, true>(g, out, s, counter, stream);
+    return seed ? generate_t<uint64_t, true, true>(g, out, s, counter, stream)
+                : generate_t<uint64_t, false, true>(g, out, s, counter, stream);
+  }
+  if (r32) return seed ? generate_t<uint32_t, true, false>(g, out, s, counter, stream)
+                       : generate_t<uint32_t, false, false>(g, out, s, counter, stream);
+  return seed ? generate_t<uint64_t, true, false>(g, out, s, counter, stream)
+              : generate_t<uint64_t, false, false>(g, out, s, counter, stream);
 }
 
 ba_status launch_degree(const GraphDev &g_in, uint64_t node_limit, uint64_t *counts, int accumulate,
