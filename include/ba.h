@@ -128,7 +128,8 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
 /* Launch shape of the generate and degree kernels.  Zero fields mean "library default".
  *  block        threads per CTA (multiple of 32, <= 1024)
  *  ctas_per_sm  resident CTAs per SM of the persistent grid
- *  tile         edges per warp tile (power of two, 64..4096)
+ *  tile         edges per warp tile (power of two, 64..2^20); plain calls halve it,
+ *               down to 256, until every warp of the grid gets several tiles
  *  refill       0 = one thread per edge, no refill (the simple kernel);
  *               1 = warp refill every hash step (ballot/popc compaction)
  *  hist_bins    degree kernel: shared-memory histogram bins per CTA

@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/ba.h"
+#include "ba.h"  // include/ba.h, on the include path of the build
 #include "ba_device.cuh"
 
 namespace ba {

@@ -156,6 +156,11 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 
 // ----------------------------------------------------------- refill generate kernel --
 
+// Per-warp staging ring: the final position r of edge (tile offset) o is parked at
+// ring[o mod kRing] until the 256-edge chunk that holds it is complete and written out.
+constexpr uint32_t kRing = 1024;
+constexpr uint32_t kChunk = 256;
+
 template <class RT, bool HasSeed, bool Batched, bool Narrow = false>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
@@ -166,178 +171,102 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
-  RT *stage = reinterpret_cast<RT *>(smem_raw) + static_cast<size_t>(wib) * 2 * T;
+  RT *ring = reinterpret_cast<RT *>(smem_raw) + static_cast<size_t>(wib) * kRing;
   GraphDev *sg = nullptr;
   if constexpr (Batched)
-    sg = reinterpret_cast<GraphDev *>(smem_raw + static_cast<size_t>(warps) * 2 * T * sizeof(RT)) +
-         2 * wib;
+    sg = reinterpret_cast<GraphDev *>(smem_raw + static_cast<size_t>(warps) * kRing * sizeof(RT)) + wib;
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + wib;
   bool first = true;
 
-  // Loads tile t into slot `slot`; false when the launch has no tile t.
-  auto fetch = [&](int slot, uint64_t &base, uint32_t &len, int &gi) -> bool {
+  for (;;) {  // one tile of up to T edges at a time (section 2: batches of edge IDs)
     const uint64_t t = next_tile(sp, first, gwarp);
-    if (t >= sp.num_tiles) return false;
-    gi = 0;
+    if (t >= sp.num_tiles) break;
+    uint64_t base;
     if constexpr (Batched) {
-      gi = graph_of_tile(tab, t);
-      copy_graph(sg + slot, tab.graphs + gi);
-      base = sg[slot].begin + ((t - sg[slot].tile0) << shift);
-      len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), sg[slot].end - base));
+      copy_graph(sg, tab.graphs + graph_of_tile(tab, t));
+      base = sg->begin + ((t - sg->tile0) << shift);
     } else {
       base = g0.begin + (t << shift);
-      len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g0.end - base));
     }
-    return true;
-  };
-  auto flush = [&](int slot, uint64_t base, uint32_t len) {
-    if constexpr (Batched)
-      flush_tile<RT, HasSeed>(stage + (slot << shift), base, len, sg[slot], out);
-    else
-      flush_tile<RT, HasSeed, Narrow>(stage + (slot << shift), base, len, g0, out);
-  };
-
-  // Warp-uniform slot state: `cur` is the tile being handed out, `oth` the older one.
-  int cur = 0, oth = 1;
-  uint64_t cur_base = 0, oth_base = 0;
-  uint32_t cur_len = 0, oth_len = 0, hoff = 0;
-  bool oth_live = false, tiles_left = true;
-  int cur_gi = 0, oth_gi = 0;
-  if (!fetch(cur, cur_base, cur_len, cur_gi)) return;
-  // What a lane needs to start edge cur_base + o: position r = cur_r0 + 2o, stage slot
-  // cur_s0 + o, and (batched) the seed and seed size of the tile's graph.
-  RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
-  uint32_t cur_s0 = static_cast<uint32_t>(cur) << shift;
-  uint64_t cur_spre = g0.seed_pre;
-  RT cur_2m0 = seed_limit<RT>(g0.two_m0), oth_2m0 = 0;
-  if constexpr (Batched) {
-    cur_spre = sg[cur].seed_pre;
-    cur_2m0 = seed_limit<RT>(sg[cur].two_m0);
-  }
-
-  // Lane state.
-  bool busy = false;
-  RT r = 0;
-  uint32_t sidx = 0;
-  uint64_t lspre = cur_spre;
-  RT l2m0 = cur_2m0;
-  bool fast = false;
-
-  // Fast steps: every lane is busy and the current tile still has >= 64 IDs to hand out,
-  // so each lane whose chain stops parks r and starts the next ID at once.  Seed: a tile
-  // in flight belongs to a graph with a seed clique; Assign: the two tiles in flight belong
-  // to different graphs, so a lane takes the current graph's constants with its new ID.
-  auto fast_loop = [&](auto seed_tag, auto assign_tag) {
-    constexpr bool Seed = decltype(seed_tag)::value;
-    constexpr bool Assign = decltype(assign_tag)::value;
-    auto step = [&]() {
-      r = hash_pre<RT>(lspre, r);
-      const bool stop = chain_stops<RT, Seed>(r, l2m0);
-      if (stop) stage[sidx] = r;
-      const uint32_t fm = __ballot_sync(kFull, stop);
-      if (stop) {
-        const uint32_t o = hoff + __popc(fm & lt);
-        sidx = cur_s0 + o;
-        r = cur_r0 + 2 * static_cast<RT>(o);
-        if constexpr (Assign) {
-          lspre = cur_spre;
-          l2m0 = cur_2m0;
-        }
-      }
-      hoff += __popc(fm);
+    const GraphDev &g = Batched ? *sg : g0;
+    const uint32_t len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - base));
+    const uint64_t spre = g.seed_pre;
+    const RT l2m0 = seed_limit<RT>(g.two_m0);
+    const RT r0 = static_cast<RT>(2 * base + 1);
+    // The rare seed lookups of the flush (clique edges, chains ending in the seed).
+    auto flush = [&](uint32_t from, uint32_t count) {
+      // ring entries from..from+count-1 are contiguous: a chunk never wraps the ring
+      flush_tile<RT, HasSeed, Narrow>(ring + (from & (kRing - 1)), base + from, count, g, out);
     };
-    do {  // two steps per bounds check: each step hands out at most 32 IDs
-      step();
-      step();
-    } while (hoff + 64 <= cur_len);
-  };
 
-  for (;;) {
-    if (fast) {
-      const bool mixed = Batched && oth_live && oth_gi != cur_gi;
-      if constexpr (HasSeed) {
-        if (cur_2m0 != 0 || (oth_live && oth_2m0 != 0)) {
-          if (mixed) fast_loop(std::true_type{}, std::true_type{});
-          else fast_loop(std::true_type{}, std::false_type{});
-        } else if (mixed) {
-          fast_loop(std::false_type{}, std::true_type{});
-        } else {
-          fast_loop(std::false_type{}, std::false_type{});
+    // Lane state: edge base+o with position r while busy.
+    uint32_t hoff = min(32u, len);
+    bool busy = static_cast<uint32_t>(lane) < hoff;
+    uint32_t o = lane;
+    RT r = r0 + 2 * static_cast<RT>(lane);
+    uint32_t flushed = 0;  // edges [0, flushed) of the tile are written out
+    bool all_busy = hoff == 32;
+
+    // Fast steps: every lane busy and >= 64 IDs may still be handed out before the ring
+    // is full or the tile ends; a lane whose chain stops parks r and starts the next ID.
+    auto fast_loop = [&](auto seed_tag) {
+      constexpr bool Seed = decltype(seed_tag)::value;
+      const uint32_t last = min(len, flushed + kRing) - 64;
+      do {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          r = hash_pre<RT>(spre, r);
+          const bool stop = chain_stops<RT, Seed>(r, l2m0);
+          if (stop) ring[o & (kRing - 1)] = r;
+          const uint32_t fm = __ballot_sync(kFull, stop);
+          if (stop) {
+            o = hoff + __popc(fm & lt);
+            r = r0 + 2 * static_cast<RT>(o);
+          }
+          hoff += __popc(fm);
         }
-      } else if (mixed) {
-        fast_loop(std::false_type{}, std::true_type{});
-      } else {
-        fast_loop(std::false_type{}, std::false_type{});
+      } while (hoff <= last);
+    };
+
+    for (;;) {
+      if (all_busy && hoff + 64 <= min(len, flushed + kRing)) {
+        if (HasSeed && l2m0 != 0) fast_loop(std::true_type{});
+        else fast_loop(std::false_type{});
       }
-    }
-    // General step: lanes may be idle, the tile may run out, tiles change here.
-    if (busy) {
-      r = hash_pre<RT>(lspre, r);
-      if (chain_stops<RT, HasSeed>(r, l2m0)) {
-        stage[sidx] = r;
-        busy = false;
+      // Make room: write out the oldest chunks whose edges are all done.
+      while (flushed + kChunk <= hoff && !__any_sync(kFull, busy && o < flushed + kChunk)) {
+        flush(flushed, kChunk);
+        flushed += kChunk;
       }
-    }
-    const uint32_t fm = __ballot_sync(kFull, !busy);
-    const uint32_t nfree = __popc(fm);
-    const uint32_t rank = __popc(fm & lt);
-    uint32_t taken = 0;
-    while (taken < nfree) {
-      const uint32_t avail = cur_len - hoff;
-      if (avail > 0) {
-        const uint32_t k = min(avail, nfree - taken);
-        if (!busy && rank - taken < k) {
-          const uint32_t o = hoff + (rank - taken);
-          sidx = cur_s0 + o;
-          r = cur_r0 + 2 * static_cast<RT>(o);
-          lspre = cur_spre;
-          l2m0 = cur_2m0;
-          busy = true;
+      if (hoff == len && !__any_sync(kFull, busy)) break;  // tile done
+      // General step: some lanes idle, or the ring or the tile is nearly used up.
+      if (busy) {
+        r = hash_pre<RT>(spre, r);
+        if (chain_stops<RT, HasSeed>(r, l2m0)) {
+          ring[o & (kRing - 1)] = r;
+          busy = false;
         }
-        hoff += k;
-        taken += k;
-        continue;
       }
-      if (!tiles_left) break;
-      if (oth_live) {
-        // The older slot is reused only after its last chain has stopped.
-        if (__any_sync(kFull, busy && (sidx >> shift) == static_cast<uint32_t>(oth))) break;
-        flush(oth, oth_base, oth_len);
-        oth_live = false;
+      const uint32_t fm = __ballot_sync(kFull, !busy);
+      const uint32_t room = min(len, flushed + kRing) - hoff;
+      const uint32_t k = min(room, static_cast<uint32_t>(__popc(fm)));
+      const uint32_t rank = __popc(fm & lt);
+      if (!busy && rank < k) {
+        o = hoff + rank;
+        r = r0 + 2 * static_cast<RT>(o);
+        busy = true;
       }
-      uint64_t nb;
-      uint32_t nl;
-      int ngi;
-      if (!fetch(oth, nb, nl, ngi)) {
-        tiles_left = false;
-        break;
-      }
-      oth_base = cur_base;
-      oth_len = cur_len;
-      oth_gi = cur_gi;
-      oth_2m0 = cur_2m0;
-      oth_live = true;
-      const int tmp = cur;
-      cur = oth;
-      oth = tmp;
-      cur_base = nb;
-      cur_len = nl;
-      cur_gi = ngi;
-      hoff = 0;
-      cur_r0 = static_cast<RT>(2 * cur_base + 1);
-      cur_s0 = static_cast<uint32_t>(cur) << shift;
-      if constexpr (Batched) {
-        cur_spre = sg[cur].seed_pre;
-        cur_2m0 = seed_limit<RT>(sg[cur].two_m0);
-      }
+      hoff += k;
+      all_busy = __ballot_sync(kFull, !busy) == 0;
     }
-    const uint32_t idle = __ballot_sync(kFull, !busy);
-    if (!tiles_left && idle == kFull) break;
-    fast = idle == 0 && hoff + 64 <= cur_len;
+    while (flushed < len) {  // the rest, chunk by chunk (a chunk never wraps the ring)
+      const uint32_t c = min(kChunk, len - flushed);
+      flush(flushed, c);
+      flushed += c;
+    }
+    __syncwarp();
   }
-  if (oth_live) flush(oth, oth_base, oth_len);
-  flush(cur, cur_base, cur_len);
 }
 
 // ------------------------------------------------------------------ degree kernels --
@@ -605,20 +534,25 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
     g_kernel_count = 1;
     return check_launch("k_generate_simple");
   }
-  const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int warps = block / 32;
-  const size_t smem = static_cast<size_t>(warps) * 2 * (size_t{1} << shift) * sizeof(RT);
+  const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT);
   auto kernel = k_generate_refill<RT, HasSeed, false, Narrow>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
+  // Tiles of the tuned size, halved (down to 256) until every warp of a full grid has
+  // about four, so that short ranges still spread over the whole GPU.
+  int grid = 0;
+  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, ~0ull, &grid);
+  if (st != BA_OK) return st;
+  uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
+  const uint64_t all_warps = static_cast<uint64_t>(grid) * warps;
+  while (shift > 8 && (len >> shift) < 4 * all_warps) --shift;
   SchedParams sp{};
   sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
   sp.counter = counter;
   sp.tile_shift = shift;
   sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
-  int grid = 0;
-  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
-  if (st != BA_OK) return st;
+  grid = static_cast<int>(std::min<uint64_t>(grid, (sp.num_tiles + warps - 1) / warps));
   sp.total_warps = static_cast<uint32_t>(grid) * warps;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -640,7 +574,6 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
     k_degree_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, hit_pos, node_limit, counts);
     return check_launch("k_degree_simple");
   }
-  const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
@@ -648,14 +581,18 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   auto kernel = k_degree_refill<RT, HasSeed>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
+  int grid = 0;
+  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, ~0ull, &grid);
+  if (st != BA_OK) return st;
+  uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
+  const uint64_t all_warps = static_cast<uint64_t>(grid) * warps;
+  while (shift > 8 && (len >> shift) < 4 * all_warps) --shift;  // as for generate
   SchedParams sp{};
   sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
   sp.counter = counter;
   sp.tile_shift = shift;
   sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
-  int grid = 0;
-  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, (sp.num_tiles + warps - 1) / warps, &grid);
-  if (st != BA_OK) return st;
+  grid = static_cast<int>(std::min<uint64_t>(grid, (sp.num_tiles + warps - 1) / warps));
   sp.total_warps = static_cast<uint32_t>(grid) * warps;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -669,8 +606,8 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
   const uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
   const int block = s.block;
   const int warps = block / 32;
-  const size_t smem = static_cast<size_t>(warps) * 2 * (size_t{1} << shift) * sizeof(RT) +
-                      static_cast<size_t>(warps) * 2 * sizeof(GraphDev);
+  const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
+                      static_cast<size_t>(warps) * sizeof(GraphDev);
   auto kernel = k_generate_refill<RT, HasSeed, true>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;

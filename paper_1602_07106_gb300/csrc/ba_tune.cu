@@ -39,7 +39,7 @@ Shape default_shape(int kind) {
       s.block = 512; s.ctas_per_sm = 2; s.tile = 2048; s.refill = 1; s.hist_bins = 12288;
       break;
     default:  // generate and batch
-      s.block = 256; s.ctas_per_sm = 4; s.tile = 512; s.refill = 1; s.hist_bins = 0;
+      s.block = 256; s.ctas_per_sm = 4; s.tile = 16384; s.refill = 1; s.hist_bins = 0;
       break;
   }
   return s;
@@ -71,7 +71,7 @@ bool valid_shape(const Shape &s, int kind) {
   if (s.ctas_per_sm < 1 || s.ctas_per_sm > 32) return false;
   if (s.refill != 0 && s.refill != 1) return false;
   if (s.refill == 1 || kind == BA_KIND_BATCH) {
-    if (s.tile < 64 || s.tile > 4096 || (s.tile & (s.tile - 1)) != 0) return false;
+    if (s.tile < 64 || s.tile > (1 << 20) || (s.tile & (s.tile - 1)) != 0) return false;
   }
   if (s.hist_bins < 0 || s.hist_bins > 28 * 1024) return false;
   if (s.hist_agg != 0 && s.hist_agg != 1) return false;
@@ -144,7 +144,7 @@ ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out) {
   }
   Shape s = from_public(*t, kind);
   if (!valid_shape(s, kind)) {
-    set_error("invalid launch shape (block multiple of 32 <= 1024, tile power of two 64..4096, "
+    set_error("invalid launch shape (block multiple of 32 <= 1024, tile power of two 64..2^20, "
               "refill 0 or 1, hist_bins <= 28672, hist_agg 0 or 1)");
     return BA_ERR_INVALID_ARG;
   }
@@ -194,7 +194,7 @@ ba_status time_median(F fn, cudaStream_t stream, int reps, float *ms) {
 std::vector<Shape> candidates(int kind) {
   std::vector<Shape> out;
   const int blocks[] = {128, 256, 512};
-  const int tiles[] = {256, 512, 1024};
+  const int tiles[] = {1024, 4096, 16384, 65536};
   if (kind == BA_KIND_DEGREE) {
     const int dblocks[] = {256, 512, 1024};
     const int bins[] = {4096, 8192, 12288, 24576};
