@@ -98,8 +98,12 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
   if constexpr (sizeof(RT) == 4) {
     // 32-bit positions: i < 2^31 and every node ID < 2^32, so the pairs are built from
     // 32-bit words (high words zero).
+    // The graph's constants in registers (in a batched launch `g` lives in shared memory).
     const uint32_t n0 = static_cast<uint32_t>(g.n0);
     const uint32_t m0 = static_cast<uint32_t>(g.m0);
+    const uint32_t seed_m0 = g.m0 > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(g.m0);
+    const uint32_t two_m0 = seed_limit<uint32_t>(g.two_m0);
+    const FastDiv dv = g.div;
     const uint32_t b32 = static_cast<uint32_t>(base);
     int4 *dst = reinterpret_cast<int4 *>(out) + out0;
     int2 *dst2 = reinterpret_cast<int2 *>(out) + out0;
@@ -107,35 +111,40 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     auto body = [&](auto pow2_tag) {
       constexpr bool Pow2 = decltype(pow2_tag)::value;
       auto div = [&](uint32_t x) -> uint32_t {
-        if constexpr (Pow2) return x >> g.div.l;
-        else return div32(x, g.div);
+        if constexpr (Pow2) return x >> dv.l;
+        else return div32(x, dv);
       };
-#pragma unroll 4
-      for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
-        const uint32_t i = b32 + j;
-        const uint32_t r = stage[j];
-        uint32_t u = n0 + div(i - m0);
-        uint32_t v = n0 + div((r >> 1) - m0);
-        if constexpr (HasSeed) {
-          // Seed edges and chains that stopped inside the seed are rare: look them up
-          // behind a warp vote so the common case never pays for the clique arithmetic.
-          const bool seed_edge = i < g.m0, seed_target = r < g.two_m0;
-          if (__any_sync(__activemask(), seed_edge || seed_target)) {
-            if (seed_edge) {
-              u = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i)));
-              v = static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1));
-            } else if (seed_target) {
-              v = static_cast<uint32_t>(clique_position(r));
-            }
-          }
-        }
+      auto put = [&](uint32_t j, uint32_t u, uint32_t v) {
         if constexpr (Narrow)
           __stcs(dst2 + j, make_int2(static_cast<int>(u), static_cast<int>(v)));
         else
           __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
+      };
+      [[maybe_unused]] bool seed_seen = false;
+#pragma unroll 4
+      for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+        const uint32_t i = b32 + j;
+        const uint32_t r = stage[j];
+        if constexpr (HasSeed) seed_seen |= r < two_m0;
+        put(j, n0 + div(i - m0), n0 + div((r >> 1) - m0));
+      }
+      if constexpr (HasSeed) {
+        // Seed edges (the first m0 of the graph) and chains that stopped inside the seed
+        // are rare: a second pass over the chunk rewrites just those pairs.
+        if (__any_sync(kFull, seed_seen) || b32 < seed_m0) {
+          for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+            const uint32_t i = b32 + j;
+            const uint32_t r = stage[j];
+            if (i < seed_m0)
+              put(j, static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i))),
+                  static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1)));
+            else if (r < two_m0)
+              put(j, n0 + div(i - m0), static_cast<uint32_t>(clique_position(r)));
+          }
+        }
       }
     };
-    if (g.div.pow2) body(std::true_type{});
+    if (dv.pow2) body(std::true_type{});
     else body(std::false_type{});
   } else {
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
