@@ -121,12 +121,23 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
           __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       };
       [[maybe_unused]] bool seed_seen = false;
+      if (!HasSeed && n0 == 0) {
+        // Empty seed graph: source i/d, target (r/2)/d; with d = 2^l both are one shift.
+        const uint32_t l1 = dv.l + 1;
 #pragma unroll 4
-      for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
-        const uint32_t i = b32 + j;
-        const uint32_t r = stage[j];
-        if constexpr (HasSeed) seed_seen |= r < two_m0;
-        put(j, n0 + div(i - m0), n0 + div((r >> 1) - m0));
+        for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+          const uint32_t r = stage[j];
+          if constexpr (Pow2) put(j, (b32 + j) >> dv.l, r >> l1);
+          else put(j, div(b32 + j), div(r >> 1));
+        }
+      } else {
+#pragma unroll 4
+        for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+          const uint32_t i = b32 + j;
+          const uint32_t r = stage[j];
+          if constexpr (HasSeed) seed_seen |= r < two_m0;
+          put(j, n0 + div(i - m0), n0 + div((r >> 1) - m0));
+        }
       }
       if constexpr (HasSeed) {
         // Seed edges (the first m0 of the graph) and chains that stopped inside the seed

@@ -321,11 +321,11 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
     if (kind == BA_KIND_GENERATE) {
       cst = time_median([&] { return launch_generate(g, scratch_dev, cand,
                                                      static_cast<unsigned long long *>(counter), s); },
-                        s, 3, &ms);
+                        s, 5, &ms);
     } else if (kind == BA_KIND_DEGREE) {
       cst = time_median([&] { return launch_degree(g, node_limit, static_cast<uint64_t *>(counts), 0,
                                                    cand, static_cast<unsigned long long *>(counter), s); },
-                        s, 3, &ms);
+                        s, 5, &ms);
     } else {
       // tile prefix depends on the candidate's tile size
       std::vector<GraphDev> gs = graphs;
@@ -342,7 +342,7 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
       BatchTable tab{dg, dp, static_cast<int32_t>(gs.size())};
       cst = time_median([&] { return launch_batch(tab, prefix.back(), r32, n0 > 1, scratch_dev, cand,
                                                   static_cast<unsigned long long *>(counter), s); },
-                        s, 3, &ms);
+                        s, 5, &ms);
     }
     if (cst == BA_ERR_CUDA) {
       st = cst;
