@@ -312,6 +312,10 @@ def gpu_arm(args):
                                      None, stream)
         tuned["batch"] = ba.ba_tune(ba.BA_KIND_BATCH, g.seed, n_total, g.d, 0, a1 - smp, a1, out,
                                     stream)
+        if not args.no_extras:  # the streaming workload runs on the 64-bit position path
+            hs = W.STREAM_HUGE
+            tuned["degree_64bit"] = ba.ba_tune(ba.BA_KIND_DEGREE, hs.seed, hs.n, hs.d, 0, hs.m // 2,
+                                               hs.m // 2 + smp, None, stream)
 
     def step(ev=None):
         if ev:

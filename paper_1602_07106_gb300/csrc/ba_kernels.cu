@@ -366,6 +366,9 @@ __device__ __forceinline__ void histogram_add(bool hit, uint64_t v, unsigned lon
     atomicAdd(bins + v, static_cast<unsigned long long>(__popc(peers)));
 }
 
+// Entries of the per-warp ring of stopped positions that may hit a counted node.
+constexpr uint32_t kHitRing = 128;
+
 // One end point at node v from the calling lane alone: a shared-memory bin below `hot`,
 // else the global counter.
 __device__ __forceinline__ void histogram_add_lane(uint64_t v, unsigned long long *bins, uint32_t hot,
@@ -389,39 +392,23 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
-
-  uint64_t cur_base = 0;
-  uint32_t cur_len = 0, hoff = 0;
-  bool tiles_left = true;
-  {
-    const uint64_t t = next_tile(sp, first, gwarp);
-    if (t < sp.num_tiles) {
-      cur_base = g.begin + (t << shift);
-      cur_len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - cur_base));
-    } else {
-      tiles_left = false;
-    }
-  }
   const uint64_t spre = g.seed_pre;
   const bool agg = sp.hist_agg != 0;
   // Only a chain that stops below hit_pos can name a node below node_limit.  As a 32-bit
   // position, hit_pos >= 2^32 saturates (every stopped 32-bit position is below it).
   const RT hp = (sizeof(RT) == 4 && hit_pos > 0xffffffffull) ? static_cast<RT>(0xffffffffu)
                                                              : static_cast<RT>(hit_pos);
-  RT cur_r0 = static_cast<RT>(2 * cur_base + 1);
-  bool busy = false, fast = false;
-  RT r = 0;
 
-  // Stopped positions below hp wait in a per-warp ring of 64; once 32 have gathered the
-  // whole warp resolves them together (one target per lane) and counts them.
-  RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * 64;
+  // Stopped positions below hp wait in a per-warp ring of kHitRing; once 32 have gathered
+  // the whole warp resolves them together (one target per lane) and counts them.
+  RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * kHitRing;
   uint32_t qhead = 0, qtail = 0;  // warp-uniform
   auto drain = [&](uint32_t k) {  // ring entries qhead .. qhead+k-1, k <= 32
     __syncwarp();
     bool hit = static_cast<uint32_t>(lane) < k;
     uint64_t v = 0;
     if (hit) {
-      v = target_of<RT, HasSeed>(ring[(qhead + lane) & 63], g);
+      v = target_of<RT, HasSeed>(ring[(qhead + lane) & (kHitRing - 1)], g);
       hit = v < node_limit;
     }
     if (agg) histogram_add(hit, v, bins, hot, counts);
@@ -429,70 +416,73 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     qhead += k;
     __syncwarp();
   };
-  auto count_hits = [&](bool stop) {
-    const bool hit = stop && r < hp;
-    const uint32_t hm = __ballot_sync(kFull, hit);
-    if (hm) {
-      if (hit) ring[(qtail + __popc(hm & lt)) & 63] = r;
-      qtail += __popc(hm);
-      if (qtail - qhead >= 32) drain(32);
-    }
-  };
-  // Fast step: every lane busy, >= 32 IDs left in the tile.
-  auto fast_step = [&]() {
-    r = hash_pre<RT>(spre, r);
-    const bool stop = chain_stops<RT, HasSeed>(r, two_m0);
-    count_hits(stop);
-    const uint32_t fm = __ballot_sync(kFull, stop);
-    if (stop) r = cur_r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
-    hoff += __popc(fm);
-  };
 
-  for (;;) {
-    if (fast) {
-      do {  // two steps per bounds check
-        fast_step();
-        fast_step();
-      } while (hoff + 64 <= cur_len);
-    }
-    bool stop = false;
-    if (busy) {
-      r = hash_pre<RT>(spre, r);
-      stop = chain_stops<RT, HasSeed>(r, two_m0);
-    }
-    count_hits(stop);
-    if (stop) busy = false;
-    const uint32_t fm = __ballot_sync(kFull, !busy);
-    const uint32_t nfree = __popc(fm);
-    const uint32_t rank = __popc(fm & lt);
-    uint32_t taken = 0;
-    while (tiles_left && taken < nfree) {
-      const uint32_t avail = cur_len - hoff;
-      if (avail > 0) {
-        const uint32_t k = min(avail, nfree - taken);
-        if (!busy && rank - taken < k) {
-          r = cur_r0 + 2 * static_cast<RT>(hoff + (rank - taken));
-          busy = true;
+  for (;;) {  // one tile at a time
+    const uint64_t t = next_tile(sp, first, gwarp);
+    if (t >= sp.num_tiles) break;
+    const uint64_t base = g.begin + (t << shift);
+    const uint32_t len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - base));
+    const RT r0 = static_cast<RT>(2 * base + 1);
+    uint32_t hoff = min(32u, len);
+    bool busy = static_cast<uint32_t>(lane) < hoff;
+    RT r = r0 + 2 * static_cast<RT>(lane);
+    bool all_busy = hoff == 32;
+
+    // Fast steps: every lane busy and >= 64 IDs left.  A stopped chain below hp is parked
+    // in the ring, which is drained as soon as 32 entries wait: a step adds at most 32, so
+    // it never holds more than 63.
+    auto fast_loop = [&](auto seed_tag) {
+      constexpr bool Seed = decltype(seed_tag)::value;
+      const uint32_t last = len - 64;
+      do {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          r = hash_pre<RT>(spre, r);
+          const bool stop = chain_stops<RT, Seed>(r, two_m0);
+          const bool hit = stop && r < hp;
+          const uint32_t hm = __ballot_sync(kFull, hit);
+          if (hm) {  // most steps have no hit at all
+            if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = r;
+            qtail += __popc(hm);
+            if (qtail - qhead >= 32) drain(32);  // leaves < 32 pending
+          }
+          const uint32_t fm = __ballot_sync(kFull, stop);
+          if (stop) r = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
+          hoff += __popc(fm);
         }
-        hoff += k;
-        taken += k;
-        continue;
+      } while (hoff <= last);
+    };
+
+    for (;;) {
+      if (all_busy && hoff + 64 <= len) {
+        if (HasSeed && two_m0 != 0) fast_loop(std::true_type{});
+        else fast_loop(std::false_type{});
       }
-      const uint64_t t = next_tile(sp, first, gwarp);
-      if (t >= sp.num_tiles) {
-        tiles_left = false;
-        break;
+      if (hoff == len && !__any_sync(kFull, busy)) break;  // tile done
+      // General step: some lanes idle, or fewer than 64 IDs left.
+      bool stop = false;
+      if (busy) {
+        r = hash_pre<RT>(spre, r);
+        stop = chain_stops<RT, HasSeed>(r, two_m0);
       }
-      cur_base = g.begin + (t << shift);
-      cur_len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - cur_base));
-      cur_r0 = static_cast<RT>(2 * cur_base + 1);
-      hoff = 0;
+      const bool hit = stop && r < hp;
+      const uint32_t hm = __ballot_sync(kFull, hit);
+      if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = r;
+      qtail += __popc(hm);
+      while (qtail - qhead >= 32) drain(32);
+      if (stop) busy = false;
+      const uint32_t fm = __ballot_sync(kFull, !busy);
+      const uint32_t k = min(len - hoff, static_cast<uint32_t>(__popc(fm)));
+      const uint32_t rank = __popc(fm & lt);
+      if (!busy && rank < k) {
+        r = r0 + 2 * static_cast<RT>(hoff + rank);
+        busy = true;
+      }
+      hoff += k;
+      all_busy = __ballot_sync(kFull, !busy) == 0;
     }
-    const uint32_t idle = __ballot_sync(kFull, !busy);
-    if (!tiles_left && idle == kFull) break;
-    fast = idle == 0 && hoff + 64 <= cur_len;
   }
-  if (qtail != qhead) drain(qtail - qhead);
+  while (qtail != qhead) drain(min(32u, qtail - qhead));
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
     const unsigned long long c = bins[b];
@@ -597,7 +587,7 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
-                      static_cast<size_t>(warps) * 64 * sizeof(RT);  // bins + hit rings
+                      static_cast<size_t>(warps) * kHitRing * sizeof(RT);  // bins + hit rings
   auto kernel = k_degree_refill<RT, HasSeed>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;

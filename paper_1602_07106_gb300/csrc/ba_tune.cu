@@ -36,7 +36,7 @@ Shape default_shape(int kind) {
   Shape s;
   switch (kind) {
     case BA_KIND_DEGREE:
-      s.block = 512; s.ctas_per_sm = 2; s.tile = 2048; s.refill = 1; s.hist_bins = 12288;
+      s.block = 512; s.ctas_per_sm = 2; s.tile = 65536; s.refill = 1; s.hist_bins = 12288;
       break;
     default:  // generate and batch
       s.block = 256; s.ctas_per_sm = 4; s.tile = 16384; s.refill = 1; s.hist_bins = 0;
