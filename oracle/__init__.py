@@ -65,6 +65,24 @@ def _load():
         lib.ora_degree_count_range.restype = ctypes.c_int
         lib.ora_degree_count_range.argtypes = [_u64, _u64, _u32, _u64, _u64, _u64, _u64,
                                                _ptr]
+        lib.ora_crc32c_update.restype = _u32
+        lib.ora_crc32c_update.argtypes = [_u32, _ptr, _u64]
+        lib.ora_crc32c_u64.restype = _u32
+        lib.ora_crc32c_u64.argtypes = [_u32, _u64]
+        lib.ora_hash_crc_bits.restype = _u64
+        lib.ora_hash_crc_bits.argtypes = [_u64, _u64]
+        lib.ora_draw.restype = _u64
+        lib.ora_draw.argtypes = [ctypes.c_int, _u64, _u64, _u64]
+        lib.ora_bb_array_variant.restype = ctypes.c_int
+        lib.ora_bb_array_variant.argtypes = [_u64, _u64, _u32, _u64, ctypes.c_int,
+                                             ctypes.c_int, _ptr]
+        lib.ora_edges_range_variant.restype = ctypes.c_int
+        lib.ora_edges_range_variant.argtypes = [_u64, _u64, _u32, _u64, ctypes.c_int,
+                                                ctypes.c_int, _u64, _u64, _ptr]
+        lib.ora_degree_count_range_variant.restype = ctypes.c_int
+        lib.ora_degree_count_range_variant.argtypes = [_u64, _u64, _u32, _u64,
+                                                       ctypes.c_int, ctypes.c_int, _u64,
+                                                       _u64, _u64, _ptr]
         _lib = lib
         return lib
 
@@ -136,4 +154,67 @@ def degree_count_range(seed: int, n: int, d: int, n0: int, a: int, b: int,
     assert counts.dtype == np.uint64 and counts.size == node_limit
     _check(_load().ora_degree_count_range(seed, n, d, n0, a, b, node_limit, _p(counts)),
            "degree_count_range")
+    return counts
+
+
+# ---------------------------------------------------------------- variants (section 4,
+# Fig. 3).  family: HASH_SPLITMIX (the h above) or HASH_CRC (hash_crc of Fig. 3);
+# no_self_loops: draw edge i's target only from the edges of earlier nodes.
+
+HASH_SPLITMIX = 0
+HASH_CRC = 1
+
+
+def crc32c_update(crc: int, data: bytes) -> int:
+    """CRC-32C advanced over ``data`` from the running value ``crc`` (no inversions)."""
+    buf = np.frombuffer(bytes(data), dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    return int(_load().ora_crc32c_update(crc, _p(buf), len(data)))
+
+
+def crc32c_u64(crc: int, v: int) -> int:
+    """The 64-bit CRC32 instruction's update: the eight bytes of v, little-endian."""
+    return int(_load().ora_crc32c_u64(crc, v))
+
+
+def hash_crc_bits(seed: int, r: int) -> int:
+    """hash_crc's 64 bits for key r (Fig. 3 for seed 0)."""
+    return int(_load().ora_hash_crc_bits(seed, r))
+
+
+def draw(family: int, seed: int, key: int, rng: int) -> int:
+    """A draw in 0..rng-1 for ``key`` (h(r) is draw(HASH_SPLITMIX, seed, r, r))."""
+    return int(_load().ora_draw(family, seed, key, rng))
+
+
+def bb_array_variant(seed: int, n: int, d: int, n0: int, family: int,
+                     no_self_loops: bool) -> np.ndarray:
+    """The full variant array E[0..2m-1] (int64)."""
+    m = num_edges(n, d, n0)
+    if m == 0:
+        raise ValueError("oracle bb_array_variant: invalid graph parameters")
+    E = np.empty(2 * m, dtype=np.int64)
+    _check(_load().ora_bb_array_variant(seed, n, d, n0, family, int(no_self_loops), _p(E)),
+           "bb_array_variant")
+    return E
+
+
+def edges_range_variant(seed: int, n: int, d: int, n0: int, family: int,
+                        no_self_loops: bool, a: int, b: int) -> np.ndarray:
+    """Edges a..b-1 of the variant graph, shape (b-a, 2), recomputed without the array."""
+    out = np.empty((max(b - a, 0), 2), dtype=np.int64)
+    _check(_load().ora_edges_range_variant(seed, n, d, n0, family, int(no_self_loops), a,
+                                           b, _p(out)), "edges_range_variant")
+    return out
+
+
+def degree_count_range_variant(seed: int, n: int, d: int, n0: int, family: int,
+                               no_self_loops: bool, a: int, b: int, node_limit: int,
+                               counts: np.ndarray | None = None) -> np.ndarray:
+    """Degrees of nodes 0..node_limit-1 over edges a..b-1 of the variant graph."""
+    if counts is None:
+        counts = np.zeros(node_limit, dtype=np.uint64)
+    assert counts.dtype == np.uint64 and counts.size == node_limit
+    _check(_load().ora_degree_count_range_variant(seed, n, d, n0, family,
+                                                  int(no_self_loops), a, b, node_limit,
+                                                  _p(counts)), "degree_count_range_variant")
     return counts

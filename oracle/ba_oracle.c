@@ -21,6 +21,10 @@
  *       seed XOR (r * 0x9E3779B97F4A7C15 mod 2^64),
  *   h = floor(z * r / 2^64)   (Lemire's multiply-shift reduction to 0..r-1).
  *
+ * Variants (the second half of this file): hash_crc of Fig. 3 (CRC-32C of r twice, then
+ * the remainder mod r) in place of h, and the self-loop-free graph of section 4, where
+ * the draw for edge i ranges only over the positions of the edges of earlier nodes.
+ *
  * Errors: every entry point returns 0 on success and a negative value when the
  * parameters do not describe a graph (d = 0, n0 > n, n = 0, 2m + 1 >= 2^64, or an
  * edge range outside 0..m).  Buffers belong to the caller.
@@ -197,6 +201,174 @@ int ora_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
     for (uint64_t i = a; i < b; i++) {
         uint64_t u = (uint64_t)position_value(seed, d, n0, m0, 2 * i, NULL);
         uint64_t v = (uint64_t)position_value(seed, d, n0, m0, 2 * i + 1, NULL);
+        if (u < node_limit) counts[u] += 1;
+        if (v < node_limit) counts[v] += 1;
+    }
+    return 0;
+}
+
+/* ================================================================================== */
+/* Variants of section 4 and Fig. 3.  Written separately from the functions above so  */
+/* that the plain array stays exactly as pinned; the plain case is reached again with  */
+/* family ORA_HASH_SPLITMIX and no_self_loops = 0.                                     */
+/* ================================================================================== */
+
+#define ORA_HASH_SPLITMIX 0
+#define ORA_HASH_CRC 1
+
+/*
+ * CRC-32C (Castagnoli polynomial x^32 + x^28 + x^27 + ... + 1, 0x1EDC6F41; bit-reflected
+ * form 0x82F63B78), advanced over len bytes starting from the running value crc, with no
+ * inversion before or after.  This is the update the SSE 4.2 CRC32 instruction performs
+ * (Fig. 3 calls it through _mm_crc32_u64).  One bit at a time, least significant first.
+ */
+uint32_t ora_crc32c_update(uint32_t crc, const uint8_t *p, uint64_t len)
+{
+    for (uint64_t k = 0; k < len; k++) {
+        crc ^= p[k];
+        for (int bit = 0; bit < 8; bit++) {
+            if (crc & 1u) crc = (crc >> 1) ^ 0x82F63B78u;
+            else crc = crc >> 1;
+        }
+    }
+    return crc;
+}
+
+/* The 64-bit form: the eight bytes of v in memory (little-endian) order. */
+uint32_t ora_crc32c_u64(uint32_t crc, uint64_t v)
+{
+    uint8_t bytes[8];
+    for (int k = 0; k < 8; k++) bytes[k] = (uint8_t)(v >> (8 * k));
+    return ora_crc32c_update(crc, bytes, 8);
+}
+
+/*
+ * The 64 bits hash_crc draws for key r (Fig. 3): CRC32 of r twice with two seeds, the
+ * first result in the high half.  Fig. 3 uses the seeds 0 and 1; here they are the low
+ * half of the user seed and the high half XOR 1, which is Fig. 3 exactly for seed 0.
+ */
+uint64_t ora_hash_crc_bits(uint64_t seed, uint64_t r)
+{
+    uint32_t c0 = (uint32_t)seed;
+    uint32_t c1 = (uint32_t)(seed >> 32) ^ 1u;
+    uint64_t hash = (uint64_t)ora_crc32c_u64(c0, r) << 32;
+    hash += ora_crc32c_u64(c1, r);
+    return hash;
+}
+
+/*
+ * A draw in 0..range-1 for key `key`: the SplitMix64 bits reduced by Lemire's multiply
+ * (as h above), or hash_crc's bits reduced by the remainder, as Fig. 3 does.  The plain
+ * h(r) is the draw with key = range = r.
+ */
+uint64_t ora_draw(int family, uint64_t seed, uint64_t key, uint64_t range)
+{
+    if (family == ORA_HASH_CRC) return ora_hash_crc_bits(seed, key) % range;
+    u128 product = (u128)ora_hash_bits(seed, key) * (u128)range;
+    return (uint64_t)(product >> 64);
+}
+
+/*
+ * Range of the draw for the target position q = 2i+1 of edge i >= m0.  Plain: 0..2i, as
+ * in section 2.  Without self-loops (section 4: r starts at the first edge of the current
+ * node): only the positions of the edges before the first edge f of edge i's node,
+ * 0..2f-1, so the target is an earlier node.
+ */
+static uint64_t draw_range(int no_self_loops, uint32_t d, uint64_t n0, uint64_t m0,
+                           uint64_t q)
+{
+    if (!no_self_loops) return q;
+    uint64_t i = q / 2;
+    uint64_t node = n0 + (i - m0) / d;
+    uint64_t first = m0 + (node - n0) * d;
+    return 2 * first;
+}
+
+/* The variant parameters describe a graph: the plain checks, a known hash family, and
+ * for the self-loop-free graph a seed network with at least one edge (n0 >= 2), since
+ * the first new node has nothing else to attach to. */
+static int variant_ok(uint64_t n, uint32_t d, uint64_t n0, int family, int no_self_loops)
+{
+    if (ora_num_edges(n, d, n0) == 0) return 0;
+    if (family != ORA_HASH_SPLITMIX && family != ORA_HASH_CRC) return 0;
+    if (no_self_loops && n0 < 2) return 0;
+    return 1;
+}
+
+/*
+ * The Batagelj-Brandes array with a variant hash family and, optionally, the section 4
+ * self-loop rule:  E[2i] = n0 + floor((i - m0)/d);  E[2i+1] = E[x], x = draw(2i+1, range).
+ */
+int ora_bb_array_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, int family,
+                         int no_self_loops, int64_t *E)
+{
+    if (!variant_ok(n, d, n0, family, no_self_loops)) return -1;
+    uint64_t m = ora_num_edges(n, d, n0);
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+
+    uint64_t p = 0;
+    for (uint64_t v = 1; v < n0; v++) {
+        for (uint64_t u = 0; u < v; u++) {
+            E[p] = (int64_t)v;
+            E[p + 1] = (int64_t)u;
+            p += 2;
+        }
+    }
+    for (uint64_t i = m0; i < m; i++) {
+        E[2 * i] = (int64_t)(n0 + (i - m0) / d);
+        uint64_t range = draw_range(no_self_loops, d, n0, m0, 2 * i + 1);
+        uint64_t x = ora_draw(family, seed, 2 * i + 1, range);
+        E[2 * i + 1] = E[x];
+    }
+    return 0;
+}
+
+/* E[p] of the variant array without the array: the recomputation of section 2, with the
+ * variant's draw at every odd position on the way. */
+static int64_t variant_position_value(uint64_t seed, uint32_t d, uint64_t n0, uint64_t m0,
+                                      int family, int no_self_loops, uint64_t p)
+{
+    for (;;) {
+        if (p < 2 * m0) return seed_clique_position(p);
+        if (p % 2 == 0) return (int64_t)(n0 + (p / 2 - m0) / d);
+        uint64_t range = draw_range(no_self_loops, d, n0, m0, p);
+        p = ora_draw(family, seed, p, range);
+    }
+}
+
+/* Edges a..b-1 of the variant graph as (E[2i], E[2i+1]) pairs into out[2(b-a)]. */
+int ora_edges_range_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                            int family, int no_self_loops, uint64_t a, uint64_t b,
+                            int64_t *out)
+{
+    if (!variant_ok(n, d, n0, family, no_self_loops)) return -1;
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    for (uint64_t i = a; i < b; i++) {
+        out[2 * (i - a)] =
+            variant_position_value(seed, d, n0, m0, family, no_self_loops, 2 * i);
+        out[2 * (i - a) + 1] =
+            variant_position_value(seed, d, n0, m0, family, no_self_loops, 2 * i + 1);
+    }
+    return 0;
+}
+
+/* counts[j] += end points equal to j among edges a..b-1 of the variant graph (a
+ * self-loop counts twice), for j < node_limit: section 3's analysis on the variant. */
+int ora_degree_count_range_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                   int family, int no_self_loops, uint64_t a, uint64_t b,
+                                   uint64_t node_limit, uint64_t *counts)
+{
+    if (!variant_ok(n, d, n0, family, no_self_loops)) return -1;
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    for (uint64_t i = a; i < b; i++) {
+        uint64_t u = (uint64_t)variant_position_value(seed, d, n0, m0, family,
+                                                      no_self_loops, 2 * i);
+        uint64_t v = (uint64_t)variant_position_value(seed, d, n0, m0, family,
+                                                      no_self_loops, 2 * i + 1);
         if (u < node_limit) counts[u] += 1;
         if (v < node_limit) counts[v] += 1;
     }
