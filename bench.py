@@ -530,8 +530,43 @@ def extras(args, ba, torch, stream, main):
                      "vs_plain": (total / statistics.median(ts)) / plain_rate}
     del out_b
     torch.cuda.empty_cache()
+    ex["variants"] = variants(ba, torch, stream, main)
     ex["serving"] = serving(args, ba, torch, plain_rate)
     return ex
+
+
+def variants(ba, torch, stream, main):
+    """The variant graphs (hash_crc of Fig. 3, section 4's self-loop-free rule) on the
+    large workload's shape, and the streaming degree count with Fig. 3's hash."""
+    res = {}
+    gl = W.PLAIN_LARGE
+    plain_ms = main["kernels_ms"]["generate"]
+    cases = [("crc_hash", ba.BA_VARIANT_CRC_HASH, 0),
+             ("no_self_loops", ba.BA_VARIANT_NO_SELF_LOOPS, gl.d + 1),
+             ("crc_hash_no_self_loops", ba.BA_VARIANT_CRC_HASH | ba.BA_VARIANT_NO_SELF_LOOPS,
+              gl.d + 1)]
+    m_max = max(ba.ba_num_edges(gl.n, gl.d, n0) for _, _, n0 in cases)
+    out = torch.empty((m_max, 2), dtype=torch.int64, device="cuda")
+    for name, v, n0 in cases:
+        m = ba.ba_num_edges(gl.n, gl.d, n0)
+        call = lambda: ba.ba_generate_edges_variant(gl.seed, gl.n, gl.d, n0, 0, m, v, out, stream)
+        call()
+        ts = _time_events(call, stream, torch, 3)
+        t = statistics.median(ts)
+        res[name] = {"workload": f"n=2^27 d=16 n0={n0} seed=42, all {m} edges as int64 pairs",
+                     "edges_per_s": m / t, "ms": 1e3 * t, "vs_plain_generate": plain_ms / (1e3 * t)}
+    del out
+    torch.cuda.empty_cache()
+    g = W.STREAM_HUGE
+    b = g.m // 10
+    counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+    call = lambda: ba.ba_degree_count_variant(g.seed, g.n, g.d, 0, 0, b, NODE_LIMIT,
+                                              ba.BA_VARIANT_CRC_HASH, counts, 0, stream)
+    ts = _time_events(call, stream, torch, 2)
+    res["crc_hash_stream_degree"] = {
+        "workload": f"n=1e10 d=100 seed=7 with hash_crc, degree count of nodes < 1e5 over "
+                    f"edges [0, {b})", "edges_per_s": b / min(ts), "seconds": min(ts)}
+    return res
 
 
 def serving(args, ba, torch, plain_rate):

@@ -123,6 +123,41 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
                                 uint64_t node_limit, uint64_t *counts_dev,
                                 int accumulate, void *stream);
 
+/* ----------------------------------------------------------------------- variants -- */
+
+/* Variants of the graph, as bit flags (0 = the graph of ba_generate_edges):
+ *  BA_VARIANT_CRC_HASH       the hash of Fig. 3 (hash_crc) in place of h: CRC-32C of the
+ *                            position r (the CRC32 instruction of SSE 4.2: Castagnoli
+ *                            polynomial, no inversions, the 8 bytes of r little-endian)
+ *                            from two initial values, the first result in the high half
+ *                            of 64 bits, then the remainder modulo the draw's range.
+ *                            Fig. 3's initial values are 0 and 1; here they are the low
+ *                            32 bits of the seed and the high 32 bits XOR 1 (Fig. 3
+ *                            exactly for seed 0).
+ *  BA_VARIANT_NO_SELF_LOOPS  section 4's self-loop-free graph: the draw for the target of
+ *                            edge i (key 2i+1, as before) ranges over the positions of
+ *                            the edges before the first edge of edge i's node, so every
+ *                            target is an earlier node.  Needs n0 >= 2 (the first new
+ *                            node must have a seed edge to attach to).
+ * The flags combine.  Unknown flags, or NO_SELF_LOOPS with n0 < 2, give
+ * BA_ERR_INVALID_ARG. */
+#define BA_VARIANT_CRC_HASH 1u
+#define BA_VARIANT_NO_SELF_LOOPS 2u
+
+/* ba_generate_edges for a variant graph (same arguments, layout and errors, plus the
+ * flags).  variant = 0 is ba_generate_edges itself. */
+ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                    uint64_t edge_begin, uint64_t edge_end, uint32_t variant,
+                                    int64_t *out_dev, void *stream);
+
+/* ba_degree_count_range for a variant graph (same arguments, layout and errors, plus the
+ * flags).  With BA_VARIANT_CRC_HASH and n0 = 0 this is the analysis of section 3 run with
+ * the hash of its experiment. */
+ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                  uint64_t edge_begin, uint64_t edge_end,
+                                  uint64_t node_limit, uint32_t variant,
+                                  uint64_t *counts_dev, int accumulate, void *stream);
+
 /* ------------------------------------------------------------------ launch shapes -- */
 
 /* Launch shape of the generate and degree kernels.  Zero fields mean "library default".

@@ -25,6 +25,16 @@ def _degrees_piece(args):
     return oracle.degree_count_range(seed, n, d, n0, a, b, limit)
 
 
+def _variant_edges_piece(args):
+    seed, n, d, n0, family, no_loops, a, b = args
+    return oracle.edges_range_variant(seed, n, d, n0, family, no_loops, a, b)
+
+
+def _variant_degrees_piece(args):
+    seed, n, d, n0, family, no_loops, a, b, limit = args
+    return oracle.degree_count_range_variant(seed, n, d, n0, family, no_loops, a, b, limit)
+
+
 def default_workers() -> int:
     return max(1, min(32, os.cpu_count() or 1))
 
@@ -56,4 +66,31 @@ def degree_count_range(seed, n, d, n0, a, b, limit, workers: int | None = None) 
     jobs = [(seed, n, d, n0, x, y, limit) for x, y in _cuts(a, b, 4 * workers)]
     with mp.get_context("spawn").Pool(workers) as pool:
         parts = pool.map(_degrees_piece, jobs)
+    return np.sum(parts, axis=0, dtype=np.uint64)
+
+
+def edges_range_variant(seed, n, d, n0, family, no_loops, a, b,
+                        workers: int | None = None) -> np.ndarray:
+    """oracle.edges_range_variant over [a, b), split across processes."""
+    workers = workers or default_workers()
+    if workers == 1 or b - a < 4_000_000:
+        return oracle.edges_range_variant(seed, n, d, n0, family, no_loops, a, b)
+    oracle.build()
+    jobs = [(seed, n, d, n0, family, no_loops, x, y) for x, y in _cuts(a, b, 4 * workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_variant_edges_piece, jobs)
+    return np.concatenate(parts, axis=0)
+
+
+def degree_count_range_variant(seed, n, d, n0, family, no_loops, a, b, limit,
+                               workers: int | None = None) -> np.ndarray:
+    """oracle.degree_count_range_variant over [a, b), split across processes and summed."""
+    workers = workers or default_workers()
+    if workers == 1 or b - a < 4_000_000:
+        return oracle.degree_count_range_variant(seed, n, d, n0, family, no_loops, a, b, limit)
+    oracle.build()
+    jobs = [(seed, n, d, n0, family, no_loops, x, y, limit)
+            for x, y in _cuts(a, b, 4 * workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_variant_degrees_piece, jobs)
     return np.sum(parts, axis=0, dtype=np.uint64)

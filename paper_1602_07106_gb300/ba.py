@@ -27,6 +27,7 @@ BA_OK, BA_ERR_INVALID_ARG, BA_ERR_RANGE, BA_ERR_OVERFLOW = 0, 1, 2, 3
 BA_ERR_CUDA, BA_ERR_NOMEM, BA_ERR_TIMEOUT, BA_ERR_BUSY, BA_ERR_NOT_FOUND = 4, 5, 6, 7, 8
 BA_KIND_GENERATE, BA_KIND_DEGREE, BA_KIND_BATCH = 0, 1, 2
 BA_REQ_QUEUED, BA_REQ_RUNNING, BA_REQ_DONE, BA_REQ_FAILED = 0, 1, 2, 3
+BA_VARIANT_CRC_HASH, BA_VARIANT_NO_SELF_LOOPS = 1, 2
 
 _u64, _u32, _i32, _i64 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -74,6 +75,10 @@ _sig("ba_generate_edges32", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _v
 _sig("ba_degree_count", ctypes.c_int, _u64, _u64, _u32, _u64, _vp, _vp)
 _sig("ba_degree_count_range", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _u64, _vp,
      ctypes.c_int, _vp)
+_sig("ba_generate_edges_variant", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _u32, _vp,
+     _vp)
+_sig("ba_degree_count_variant", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _u64, _u32,
+     _vp, ctypes.c_int, _vp)
 _sig("ba_set_tuning", ctypes.c_int, _i32, ctypes.POINTER(ba_tuning))
 _sig("ba_get_tuning", ctypes.c_int, _i32, _u64, ctypes.POINTER(ba_tuning))
 _sig("ba_tune", ctypes.c_int, _i32, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _vp,
@@ -188,6 +193,22 @@ def ba_degree_count_range(seed, n, d, n0, edge_begin, edge_end, node_limit, coun
     _check(_lib.ba_degree_count_range(seed, n, d, n0, edge_begin, edge_end, node_limit,
                                       _ptr(counts), int(accumulate), _stream(stream)),
            "ba_degree_count_range")
+
+
+def ba_generate_edges_variant(seed, n, d, n0, edge_begin, edge_end, variant, out,
+                              stream=None) -> None:
+    _need_cuda(out, torch.int64, 2 * (edge_end - edge_begin), "ba_generate_edges_variant out")
+    _check(_lib.ba_generate_edges_variant(seed, n, d, n0, edge_begin, edge_end, variant,
+                                          _ptr(out), _stream(stream)),
+           "ba_generate_edges_variant")
+
+
+def ba_degree_count_variant(seed, n, d, n0, edge_begin, edge_end, node_limit, variant, counts,
+                            accumulate=0, stream=None) -> None:
+    _need_cuda(counts, torch.int64, node_limit, "ba_degree_count_variant counts")
+    _check(_lib.ba_degree_count_variant(seed, n, d, n0, edge_begin, edge_end, node_limit,
+                                        variant, _ptr(counts), int(accumulate),
+                                        _stream(stream)), "ba_degree_count_variant")
 
 
 def _tuning(t) -> ba_tuning | None:

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "ba_draw.cuh"
 #include "ba_internal.h"
 
 namespace ba {
@@ -229,6 +230,78 @@ ba_status ba_degree_count(uint64_t seed, uint64_t n, uint32_t d, uint64_t node_l
   ba_status st = validate_graph(n, d, 0, &m);
   if (st != BA_OK) return st;
   return ba_degree_count_range(seed, n, d, 0, 0, m, node_limit, counts_dev, 0, stream);
+}
+
+// Checks the variant flags against the graph: known bits only, and a seed edge for the
+// self-loop-free rule.
+static ba_status check_variant(uint32_t variant, uint64_t n0) {
+  if ((variant & ~static_cast<uint32_t>(BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS)) != 0) {
+    set_error("unknown variant flag");
+    return BA_ERR_INVALID_ARG;
+  }
+  if ((variant & BA_VARIANT_NO_SELF_LOOPS) && n0 < 2) {
+    set_error("the self-loop-free graph needs a seed graph with an edge (n0 >= 2)");
+    return BA_ERR_INVALID_ARG;
+  }
+  return BA_OK;
+}
+
+static_assert(BA_VARIANT_CRC_HASH == kVariantCrc && BA_VARIANT_NO_SELF_LOOPS == kVariantNoLoop,
+              "public variant flags and kernel policies disagree");
+
+ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                    uint64_t edge_begin, uint64_t edge_end, uint32_t variant,
+                                    int64_t *out_dev, void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  st = check_variant(variant, n0);
+  if (st != BA_OK) return st;
+  if (edge_begin == edge_end) return BA_OK;
+  if (out_dev == nullptr || (reinterpret_cast<uintptr_t>(out_dev) & 15) != 0) {
+    set_error("out must be a non-NULL, 16-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  shape.refill = 1;  // the variant draws run on the refill kernel only
+  StreamScratch scratch;
+  st = scratch.alloc(sizeof(unsigned long long), s);
+  if (st != BA_OK) return st;
+  return launch_generate_variant(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr),
+                                 s, variant);
+}
+
+ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                  uint64_t edge_begin, uint64_t edge_end, uint64_t node_limit,
+                                  uint32_t variant, uint64_t *counts_dev, int accumulate,
+                                  void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  st = check_variant(variant, n0);
+  if (st != BA_OK) return st;
+  if (node_limit == 0) return BA_OK;
+  if (counts_dev == nullptr || (reinterpret_cast<uintptr_t>(counts_dev) & 7) != 0) {
+    set_error("counts must be a non-NULL, 8-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  if (node_limit > (1ull << 40)) {
+    set_error("node_limit above 2^40 counters");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  Shape shape = shape_for(BA_KIND_DEGREE, edge_end <= (1ull << 31));
+  shape.refill = 1;
+  StreamScratch scratch;
+  st = scratch.alloc(sizeof(unsigned long long), s);
+  if (st != BA_OK) return st;
+  return launch_degree_variant(g, node_limit, counts_dev, accumulate, shape,
+                               static_cast<unsigned long long *>(scratch.ptr), s, variant);
 }
 
 ba_status ba_generate_edges_host(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,

@@ -1,0 +1,155 @@
+// ba_draw.cuh -- the random draw that the chain of Fig. 1 makes at an odd position r.
+//
+// The refill kernels are written once over a Draw policy:
+//   DrawPlain                h(r) of section 2: SplitMix64 bits of r, reduced into 0..r-1
+//                            by a multiply-high.  The library's default graph.
+//   DrawVariant<Crc, NoLoop> Crc:    the bits of Fig. 3's hash_crc (CRC-32C of r with two
+//                                    initial values, first result in the high half),
+//                                    reduced by the remainder as Fig. 3 does.
+//                            NoLoop: section 4's self-loop-free rule: the draw for
+//                                    position r = 2j+1 ranges over 0..2f-1, f the first
+//                                    edge of the node that owns edge j, so it only reaches
+//                                    edges of earlier nodes.  The key stays r.
+// Every policy maps (graph, r) to one value; the chain stops on the same test (even, or
+// a seed position) whatever the draw.
+#pragma once
+#include <cstdint>
+
+#include "ba_device.cuh"
+
+namespace ba {
+
+struct DrawPlain {
+  static constexpr bool kTables = false;
+  static constexpr bool kNeedsSeed = false;
+  uint64_t spre = 0;
+  // CTA-collective, once per kernel (nothing to prepare).
+  __device__ __forceinline__ void setup(const GraphDev &, uint32_t *, bool) {}
+  // Per tile: the graph whose positions are drawn next.
+  __device__ __forceinline__ void bind(const GraphDev &g) { spre = g.seed_pre; }
+  template <class RT>
+  __device__ __forceinline__ RT operator()(RT r) const { return hash_pre<RT>(spre, r); }
+};
+
+// CRC-32C in bit-reflected form (polynomial 0x1EDC6F41 reversed).
+constexpr uint32_t kCrc32cReflected = 0x82F63B78u;
+
+// One register step of the reflected CRC: divide by x, reduce.
+__device__ __forceinline__ uint32_t crc_shift_bit(uint32_t c) {
+  return (c >> 1) ^ (kCrc32cReflected & (0u - (c & 1u)));
+}
+
+// The CRC register after an 8-byte word whose byte k is b and all other bytes zero, from
+// a zero register.  The CRC is linear over GF(2), so the register after any word w from
+// register c is  reg_after_zero_word(c) XOR  XOR_k byte_part(k, byte k of w).
+__device__ __forceinline__ uint32_t crc_byte_part(uint32_t k, uint32_t b) {
+  uint32_t c = 0;
+  for (uint32_t pos = 0; pos < 8; ++pos) {
+    if (pos == k) c ^= b;
+    for (int bit = 0; bit < 8; ++bit) c = crc_shift_bit(c);
+  }
+  return c;
+}
+
+// The register after a zero word from register c: the initial value's share.
+__device__ __forceinline__ uint32_t crc_register_part(uint32_t c) {
+  for (int bit = 0; bit < 64; ++bit) c = crc_shift_bit(c);
+  return c;
+}
+
+// Bytes of a position that the CRC tables cover: 4 on the 32-bit path (the upper half of
+// a position < 2^32 is zero and adds nothing), 8 otherwise.
+__host__ __device__ constexpr uint32_t crc_table_bytes(bool r32) { return r32 ? 4u : 8u; }
+__host__ __device__ constexpr size_t crc_table_smem(bool r32) {
+  return static_cast<size_t>(crc_table_bytes(r32)) * 256u * sizeof(uint32_t);
+}
+
+template <bool Crc, bool NoLoop>
+struct DrawVariant {
+  static constexpr bool kTables = Crc;
+  static constexpr bool kNeedsSeed = NoLoop;  // the first new node needs a seed edge
+  uint64_t spre = 0;            // SplitMix64 draws
+  const uint32_t *tab = nullptr;  // Crc: byte_part tables, 256 entries per byte position
+  uint32_t reg_hi = 0;          // Crc: shares of the two initial values
+  uint32_t reg_lo = 0;
+  uint64_t m0 = 0;              // NoLoop: first edge of node n0, and division by d
+  FastDiv div{};
+  uint32_t d = 1;
+
+  // CTA-collective: builds the CRC tables in shared memory (all threads take part, then
+  // one __syncthreads).  Fig. 3's initial values 0 and 1 become the low half of the seed
+  // and the high half XOR 1 (Fig. 3 exactly for seed 0).
+  __device__ __forceinline__ void setup(const GraphDev &g, uint32_t *smem_tab, bool r32) {
+    if constexpr (Crc) {
+      const uint32_t entries = crc_table_bytes(r32) * 256u;
+      for (uint32_t e = threadIdx.x; e < entries; e += blockDim.x)
+        smem_tab[e] = crc_byte_part(e >> 8, e & 255u);
+      reg_hi = crc_register_part(static_cast<uint32_t>(g.seed));
+      reg_lo = crc_register_part(static_cast<uint32_t>(g.seed >> 32) ^ 1u);
+      tab = smem_tab;
+      __syncthreads();
+    }
+  }
+  __device__ __forceinline__ void bind(const GraphDev &g) {
+    spre = g.seed_pre;
+    m0 = g.m0;
+    div = g.div;
+    d = g.d;
+  }
+
+  // Range of the draw at odd position r >= 2 m0 (r itself without NoLoop).  Positions
+  // inside the seed never reach a draw that matters (their edges are rewritten from the
+  // clique); they are clamped to the first new node so the range stays >= 2 m0 >= 2.
+  template <class RT>
+  __device__ __forceinline__ RT range_of(RT r) const {
+    if constexpr (!NoLoop) {
+      return r;
+    } else if constexpr (sizeof(RT) == 4) {
+      const uint32_t m0_32 = static_cast<uint32_t>(m0);
+      const uint32_t j = max(r >> 1, m0_32);
+      return 2u * (m0_32 + d * div32(j - m0_32, div));
+    } else {
+      const uint64_t j = max(static_cast<uint64_t>(r >> 1), m0);
+      return 2 * (m0 + static_cast<uint64_t>(d) * div64(j - m0, div));
+    }
+  }
+
+  template <class RT>
+  __device__ __forceinline__ uint64_t crc_bits(RT r) const {
+    uint32_t c = tab[r & 255u] ^ tab[256u + ((r >> 8) & 255u)] ^ tab[512u + ((r >> 16) & 255u)] ^
+                 tab[768u + static_cast<uint32_t>((r >> 24) & 255u)];
+    if constexpr (sizeof(RT) == 8) {
+      const uint32_t hi = static_cast<uint32_t>(r >> 32);
+      c ^= tab[1024u + (hi & 255u)] ^ tab[1280u + ((hi >> 8) & 255u)] ^
+           tab[1536u + ((hi >> 16) & 255u)] ^ tab[1792u + (hi >> 24)];
+    }
+    return (static_cast<uint64_t>(c ^ reg_hi) << 32) | (c ^ reg_lo);
+  }
+
+  template <class RT>
+  __device__ __forceinline__ RT operator()(RT r) const {
+    const RT range = range_of<RT>(r);
+    if constexpr (Crc) {
+      return static_cast<RT>(crc_bits<RT>(r) % static_cast<uint64_t>(range));
+    } else if constexpr (sizeof(RT) == 4) {
+      // SplitMix64 bits of key r, multiply-high by the range (< 2^32), as in hash_r32_pre
+      const uint64_t p = static_cast<uint64_t>(r) * kGamma;
+      uint64_t z = (spre ^ p ^ (p >> 30)) * kMixA;
+      z = (z ^ (z >> 27)) * kMixB;
+      z ^= z >> 31;
+      const uint32_t t = __umulhi(static_cast<uint32_t>(z), range);
+      return static_cast<uint32_t>((static_cast<uint64_t>(static_cast<uint32_t>(z >> 32)) * range + t) >> 32);
+    } else {
+      const uint64_t p = r * kGamma;
+      uint64_t z = (spre ^ p ^ (p >> 30)) * kMixA;
+      z = (z ^ (z >> 27)) * kMixB;
+      z ^= z >> 31;
+      return __umul64hi(z, range);
+    }
+  }
+};
+
+// Variant flags of the public API (BA_VARIANT_*) to policy.
+enum : uint32_t { kVariantCrc = 1u, kVariantNoLoop = 2u };
+
+}  // namespace ba

@@ -57,6 +57,14 @@ ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
 ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                         int accumulate, const Shape &s, unsigned long long *counter,
                         cudaStream_t stream);
+// Variant draws (BA_VARIANT_* flags; 0 = the plain graph): int64 output.  The caller has
+// checked the flags and that the self-loop-free rule has a seed graph (n0 >= 2).
+ba_status launch_generate_variant(const GraphDev &g, int64_t *out, const Shape &s,
+                                  unsigned long long *counter, cudaStream_t stream,
+                                  uint32_t variant);
+ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                                int accumulate, const Shape &s, unsigned long long *counter,
+                                cudaStream_t stream, uint32_t variant);
 ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,
                        int64_t *out, const Shape &s, unsigned long long *counter,
                        cudaStream_t stream);

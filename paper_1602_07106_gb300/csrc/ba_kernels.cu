@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "ba_draw.cuh"
 #include "ba_internal.h"
 
 namespace ba {
@@ -181,7 +182,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 constexpr uint32_t kRing = 1024;
 constexpr uint32_t kChunk = 256;
 
-template <class RT, bool HasSeed, bool Batched, bool Narrow = false>
+template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlain>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
                   int64_t *__restrict__ out) {
@@ -195,6 +196,9 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   GraphDev *sg = nullptr;
   if constexpr (Batched)
     sg = reinterpret_cast<GraphDev *>(smem_raw + static_cast<size_t>(warps) * kRing * sizeof(RT)) + wib;
+  Draw draw;  // tables (if any) after the rings
+  draw.setup(g0, reinterpret_cast<uint32_t *>(smem_raw + static_cast<size_t>(warps) * kRing * sizeof(RT)),
+             sizeof(RT) == 4);
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + wib;
   bool first = true;
@@ -211,7 +215,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     }
     const GraphDev &g = Batched ? *sg : g0;
     const uint32_t len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - base));
-    const uint64_t spre = g.seed_pre;
+    draw.bind(g);
     const RT l2m0 = seed_limit<RT>(g.two_m0);
     const RT r0 = static_cast<RT>(2 * base + 1);
     // The rare seed lookups of the flush (clique edges, chains ending in the seed).
@@ -236,7 +240,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
       do {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          r = hash_pre<RT>(spre, r);
+          r = draw(r);
           const bool stop = chain_stops<RT, Seed>(r, l2m0);
           if (stop) ring[o & (kRing - 1)] = r;
           const uint32_t fm = __ballot_sync(kFull, stop);
@@ -262,7 +266,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
       if (hoff == len && !__any_sync(kFull, busy)) break;  // tile done
       // General step: some lanes idle, or the ring or the tile is nearly used up.
       if (busy) {
-        r = hash_pre<RT>(spre, r);
+        r = draw(r);
         if (chain_stops<RT, HasSeed>(r, l2m0)) {
           ring[o & (kRing - 1)] = r;
           busy = false;
@@ -377,13 +381,18 @@ __device__ __forceinline__ void histogram_add_lane(uint64_t v, unsigned long lon
   else atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
 }
 
-template <class RT, bool HasSeed>
+template <class RT, bool HasSeed, class Draw = DrawPlain>
 __global__ void __launch_bounds__(1024)
 k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64_t node_limit,
                 uint32_t hot, uint64_t *__restrict__ counts) {
   extern __shared__ __align__(16) unsigned long long bins[];
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) bins[b] = 0;
   __syncthreads();
+  Draw draw;  // tables (if any) after the bins and the hit rings
+  draw.setup(g, reinterpret_cast<uint32_t *>(reinterpret_cast<RT *>(bins + hot) +
+                                             static_cast<size_t>(blockDim.x >> 5) * kHitRing),
+             sizeof(RT) == 4);
+  draw.bind(g);
 
   const uint32_t shift = sp.tile_shift;
   const uint32_t T = 1u << shift;
@@ -392,7 +401,6 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
-  const uint64_t spre = g.seed_pre;
   const bool agg = sp.hist_agg != 0;
   // Only a chain that stops below hit_pos can name a node below node_limit.  As a 32-bit
   // position, hit_pos >= 2^32 saturates (every stopped 32-bit position is below it).
@@ -437,7 +445,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       do {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          r = hash_pre<RT>(spre, r);
+          r = draw(r);
           const bool stop = chain_stops<RT, Seed>(r, two_m0);
           const bool hit = stop && r < hp;
           const uint32_t hm = __ballot_sync(kFull, hit);
@@ -462,7 +470,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       // General step: some lanes idle, or fewer than 64 IDs left.
       bool stop = false;
       if (busy) {
-        r = hash_pre<RT>(spre, r);
+        r = draw(r);
         stop = chain_stops<RT, HasSeed>(r, two_m0);
       }
       const bool hit = stop && r < hp;
@@ -530,23 +538,26 @@ ba_status check_launch(const char *what) {
   return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
 }
 
-template <class RT, bool HasSeed, bool Narrow>
+template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlain>
 ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
                      cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
-  if (s.refill == 0) {
-    int grid = 0;
-    ba_status st = persistent_grid(k_generate_simple<RT, HasSeed, Narrow>, block, 0, s.ctas_per_sm,
-                                   (len + block - 1) / block, &grid);
-    if (st != BA_OK) return st;
-    k_generate_simple<RT, HasSeed, Narrow><<<grid, block, 0, stream>>>(g, out);
-    g_kernel_count = 1;
-    return check_launch("k_generate_simple");
+  if constexpr (std::is_same_v<Draw, DrawPlain>) {  // the simple kernel draws h(r) only
+    if (s.refill == 0) {
+      int grid = 0;
+      ba_status st = persistent_grid(k_generate_simple<RT, HasSeed, Narrow>, block, 0,
+                                     s.ctas_per_sm, (len + block - 1) / block, &grid);
+      if (st != BA_OK) return st;
+      k_generate_simple<RT, HasSeed, Narrow><<<grid, block, 0, stream>>>(g, out);
+      g_kernel_count = 1;
+      return check_launch("k_generate_simple");
+    }
   }
   const int warps = block / 32;
-  const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT);
-  auto kernel = k_generate_refill<RT, HasSeed, false, Narrow>;
+  const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
+                      (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
+  auto kernel = k_generate_refill<RT, HasSeed, false, Narrow, Draw>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   // Tiles of the tuned size, halved (down to 256) until every warp of a full grid has
@@ -571,24 +582,27 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
   return check_launch("k_generate_refill");
 }
 
-template <class RT, bool HasSeed>
+template <class RT, bool HasSeed, class Draw = DrawPlain>
 ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uint64_t *counts,
                    const Shape &s, unsigned long long *counter, cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
-  if (s.refill == 0) {
-    int grid = 0;
-    ba_status st = persistent_grid(k_degree_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
-                                   (len + block - 1) / block, &grid);
-    if (st != BA_OK) return st;
-    k_degree_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, hit_pos, node_limit, counts);
-    return check_launch("k_degree_simple");
+  if constexpr (std::is_same_v<Draw, DrawPlain>) {
+    if (s.refill == 0) {
+      int grid = 0;
+      ba_status st = persistent_grid(k_degree_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
+                                     (len + block - 1) / block, &grid);
+      if (st != BA_OK) return st;
+      k_degree_simple<RT, HasSeed><<<grid, block, 0, stream>>>(g, hit_pos, node_limit, counts);
+      return check_launch("k_degree_simple");
+    }
   }
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
-                      static_cast<size_t>(warps) * kHitRing * sizeof(RT);  // bins + hit rings
-  auto kernel = k_degree_refill<RT, HasSeed>;
+                      static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit rings
+                      (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
+  auto kernel = k_degree_refill<RT, HasSeed, Draw>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   int grid = 0;
@@ -659,8 +673,29 @@ ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
               : generate_t<uint64_t, false, false>(g, out, s, counter, stream);
 }
 
-ba_status launch_degree(const GraphDev &g_in, uint64_t node_limit, uint64_t *counts, int accumulate,
-                        const Shape &s, unsigned long long *counter, cudaStream_t stream) {
+namespace {
+
+// Generate with a variant draw: int64 output, refill kernel.  The self-loop-free rule
+// needs a seed graph, so it never runs without one.
+template <class Draw>
+ba_status generate_variant_t(const GraphDev &g, int64_t *out, const Shape &s,
+                             unsigned long long *counter, cudaStream_t stream, bool seed) {
+  const bool r32 = g.end <= (1ull << 31);
+  if (seed) return r32 ? generate_t<uint32_t, true, false, Draw>(g, out, s, counter, stream)
+                       : generate_t<uint64_t, true, false, Draw>(g, out, s, counter, stream);
+  if constexpr (Draw::kNeedsSeed) {
+    return BA_ERR_INVALID_ARG;
+  } else {
+    return r32 ? generate_t<uint32_t, false, false, Draw>(g, out, s, counter, stream)
+               : generate_t<uint64_t, false, false, Draw>(g, out, s, counter, stream);
+  }
+}
+
+// Degree count: closed-form sources and seed end points, then the targets of the
+// non-seed edges in range by the chain of Fig. 1 with the given draw.
+template <class Draw>
+ba_status degree_with(const GraphDev &g_in, uint64_t node_limit, uint64_t *counts, int accumulate,
+                      const Shape &s, unsigned long long *counter, cudaStream_t stream) {
   g_kernel_count = 0;
   // 1. sources and seed end points, in closed form, over all node_limit entries
   {
@@ -688,12 +723,56 @@ ba_status launch_degree(const GraphDev &g_in, uint64_t node_limit, uint64_t *cou
   const bool r32 = g.end <= (1ull << 31);
   const bool seed = g.m0 > 0;
   ba_status st;
-  if (r32) st = seed ? degree_t<uint32_t, true>(g, hit_pos, node_limit, counts, s, counter, stream)
-                     : degree_t<uint32_t, false>(g, hit_pos, node_limit, counts, s, counter, stream);
-  else st = seed ? degree_t<uint64_t, true>(g, hit_pos, node_limit, counts, s, counter, stream)
-                 : degree_t<uint64_t, false>(g, hit_pos, node_limit, counts, s, counter, stream);
+  if (seed) {
+    st = r32 ? degree_t<uint32_t, true, Draw>(g, hit_pos, node_limit, counts, s, counter, stream)
+             : degree_t<uint64_t, true, Draw>(g, hit_pos, node_limit, counts, s, counter, stream);
+  } else if constexpr (Draw::kNeedsSeed) {
+    st = BA_ERR_INVALID_ARG;
+  } else {
+    st = r32 ? degree_t<uint32_t, false, Draw>(g, hit_pos, node_limit, counts, s, counter, stream)
+             : degree_t<uint64_t, false, Draw>(g, hit_pos, node_limit, counts, s, counter, stream);
+  }
   if (st == BA_OK) g_kernel_count = 2;
   return st;
+}
+
+}  // namespace
+
+ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts, int accumulate,
+                        const Shape &s, unsigned long long *counter, cudaStream_t stream) {
+  return degree_with<DrawPlain>(g, node_limit, counts, accumulate, s, counter, stream);
+}
+
+ba_status launch_generate_variant(const GraphDev &g, int64_t *out, const Shape &s,
+                                  unsigned long long *counter, cudaStream_t stream,
+                                  uint32_t variant) {
+  g_kernel_count = 0;
+  const bool seed = g.m0 > 0;
+  switch (variant) {
+    case 0: return launch_generate(g, out, s, counter, stream, false);
+    case kVariantCrc:
+      return generate_variant_t<DrawVariant<true, false>>(g, out, s, counter, stream, seed);
+    case kVariantNoLoop:
+      return generate_variant_t<DrawVariant<false, true>>(g, out, s, counter, stream, seed);
+    case kVariantCrc | kVariantNoLoop:
+      return generate_variant_t<DrawVariant<true, true>>(g, out, s, counter, stream, seed);
+    default: return BA_ERR_INVALID_ARG;
+  }
+}
+
+ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                                int accumulate, const Shape &s, unsigned long long *counter,
+                                cudaStream_t stream, uint32_t variant) {
+  switch (variant) {
+    case 0: return degree_with<DrawPlain>(g, node_limit, counts, accumulate, s, counter, stream);
+    case kVariantCrc:
+      return degree_with<DrawVariant<true, false>>(g, node_limit, counts, accumulate, s, counter, stream);
+    case kVariantNoLoop:
+      return degree_with<DrawVariant<false, true>>(g, node_limit, counts, accumulate, s, counter, stream);
+    case kVariantCrc | kVariantNoLoop:
+      return degree_with<DrawVariant<true, true>>(g, node_limit, counts, accumulate, s, counter, stream);
+    default: return BA_ERR_INVALID_ARG;
+  }
 }
 
 ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,

@@ -72,6 +72,29 @@ def test_degree_count_argument_rules():
     ba.ba_degree_count(1, 10, 1, 0, counts=None, stream=0)          # node_limit 0: no-op
 
 
+def test_variant_argument_rules():
+    V = ba.BA_VARIANT_NO_SELF_LOOPS
+    for n0 in (0, 1):                      # the self-loop-free rule needs a seed edge
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_generate_edges_variant(1, 10, 2, n0, 0, 5, V, out=0x1000, stream=0)
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_degree_count_variant(1, 10, 2, n0, 0, 5, 8, V, counts=0x1000, stream=0)
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:   # unknown flag
+        ba.ba_generate_edges_variant(1, 10, 2, 3, 0, 5, 4, out=0x1000, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_edges_variant(1, 10, 2, 3, 0, 99, ba.BA_VARIANT_CRC_HASH, out=0x1000,
+                                     stream=0)
+    assert e.value.status == ba.BA_ERR_RANGE
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_generate_edges_variant(1, 10, 2, 3, 0, 5, 3, out=0x1008, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    ba.ba_generate_edges_variant(1, 10, 2, 3, 4, 4, 3, out=None, stream=0)    # empty: OK
+    ba.ba_degree_count_variant(1, 10, 2, 3, 0, 5, 0, 3, counts=None, stream=0)  # no counts
+
+
 def test_tuning_overrides_validate_and_round_trip(tmp_path):
     default = ba.ba_get_tuning(ba.BA_KIND_GENERATE)
     assert default["block"] % 32 == 0 and default["tile"] & (default["tile"] - 1) == 0
