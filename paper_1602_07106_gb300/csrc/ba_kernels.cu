@@ -4,20 +4,24 @@
 //   k_generate_simple  one thread per edge, grid-stride; the parity baseline.
 //   k_generate_refill  persistent warps.  Each warp takes tiles of T edge IDs from a
 //                      global counter (section 2's dynamic load balancing by batches of
-//                      edge IDs).  Every step each busy lane applies one hash; lanes whose
-//                      chain stopped park the final position r in a shared-memory slot
-//                      of the tile and take the next edge ID of the tile by ballot/popc
-//                      compaction, so the geometric chain lengths do not leave lanes
-//                      idle.  A warp keeps two tile slots: it hands out edge IDs of the
-//                      newer tile while the older tile's last chains finish.  A finished
-//                      tile is written out by the whole warp: consecutive lanes store
-//                      consecutive 16-byte (source, target) pairs.
+//                      edge IDs).  Every step each busy lane applies one draw; a lane whose
+//                      chain stopped parks the final position r in the warp's staging ring
+//                      (1024 entries, indexed by the edge's offset in the tile) and takes
+//                      the tile's next edge ID by ballot/popc compaction, so geometric
+//                      chain lengths do not leave lanes idle.  Whenever the oldest
+//                      256-edge chunk of the ring has no chain left in flight, the whole
+//                      warp writes it out: consecutive lanes store consecutive 16-byte
+//                      (source, target) pairs (8-byte int32 pairs for the narrow output).
+//                      The draw is a policy (ba_draw.cuh): h(r), or the variants.
 // Degree count (section 3's streaming analysis, no edge stored):
 //   k_degree_init      sources and seed-clique end points in closed form.
 //   k_degree_simple    one thread per edge, global atomics.
-//   k_degree_refill    the refill scheduler of k_generate_refill; targets below the
-//                      shared-memory limit go to a per-CTA histogram with warp-aggregated
-//                      atomics (__match_any_sync), the rest to global 64-bit atomics.
+//   k_degree_refill    the refill scheduler of k_generate_refill; chains that stop below
+//                      the position of the first uncounted node are parked in a per-warp
+//                      ring and counted 32 at a time: targets below the shared-memory
+//                      limit in a per-CTA 64-bit histogram (optionally one atomic per
+//                      distinct node per warp, __match_any_sync), the rest with global
+//                      64-bit atomics.
 #include <algorithm>
 #include <type_traits>
 
