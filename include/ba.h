@@ -169,7 +169,10 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
  *               1 = warp refill every hash step (ballot/popc compaction)
  *  hist_bins    degree kernel: shared-memory histogram bins per CTA
  *  hist_agg     degree kernel: 1 = one shared-memory atomic per distinct node per warp
- *               (__match_any_sync aggregation), 0 = one atomic per hitting lane */
+ *               (__match_any_sync aggregation), 0 = one atomic per hitting lane
+ *  chains       refill kernels: hash chains each lane keeps in flight (1 or 2); a
+ *               second independent chain hides the latency of the hash's dependent
+ *               multiplies */
 typedef struct ba_tuning {
     int32_t block;
     int32_t ctas_per_sm;
@@ -177,7 +180,8 @@ typedef struct ba_tuning {
     int32_t refill;
     int32_t hist_bins;
     int32_t hist_agg;
-    int32_t reserved[2];
+    int32_t chains;
+    int32_t reserved;
 } ba_tuning;
 
 /* Kernel families the tuner keys on. */

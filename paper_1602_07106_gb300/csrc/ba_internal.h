@@ -34,6 +34,7 @@ struct Shape {
   int refill = 1;
   int hist_bins = 0;
   int hist_agg = 0;
+  int chains = 1;  // hash chains per lane in the generate / batched refill kernels
 };
 
 // ---- host helpers (ba_api.cu)

@@ -186,7 +186,11 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 constexpr uint32_t kRing = 1024;
 constexpr uint32_t kChunk = 256;
 
-template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlain>
+// K chains per lane: lane l runs the chains of virtual lanes l, l+32, ..., l+32(K-1), so
+// each lane has K independent hash chains in flight.  The hash is one long dependency
+// chain of integer multiplies and shifts; a second chain per lane hides its latency.
+template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlain,
+          int K = 1>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
                   int64_t *__restrict__ out) {
@@ -205,6 +209,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
              sizeof(RT) == 4);
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + wib;
+  constexpr uint32_t kLanes = 32u * K;  // virtual lanes of the warp
   bool first = true;
 
   for (;;) {  // one tile of up to T edges at a time (section 2: batches of edge IDs)
@@ -222,71 +227,95 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     draw.bind(g);
     const RT l2m0 = seed_limit<RT>(g.two_m0);
     const RT r0 = static_cast<RT>(2 * base + 1);
-    // The rare seed lookups of the flush (clique edges, chains ending in the seed).
     auto flush = [&](uint32_t from, uint32_t count) {
       // ring entries from..from+count-1 are contiguous: a chunk never wraps the ring
       flush_tile<RT, HasSeed, Narrow>(ring + (from & (kRing - 1)), base + from, count, g, out);
     };
 
-    // Lane state: edge base+o with position r while busy.
-    uint32_t hoff = min(32u, len);
-    bool busy = static_cast<uint32_t>(lane) < hoff;
-    uint32_t o = lane;
-    RT r = r0 + 2 * static_cast<RT>(lane);
+    // Chain c of this lane: edge base+o[c] at position r[c] while busy[c].
+    uint32_t hoff = min(kLanes, len);
+    uint32_t o[K];
+    RT r[K];
+    bool busy[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      o[c] = 32u * c + lane;
+      busy[c] = o[c] < hoff;
+      r[c] = r0 + 2 * static_cast<RT>(o[c]);
+    }
     uint32_t flushed = 0;  // edges [0, flushed) of the tile are written out
-    bool all_busy = hoff == 32;
+    bool all_busy = hoff == kLanes;
 
-    // Fast steps: every lane busy and >= 64 IDs may still be handed out before the ring
-    // is full or the tile ends; a lane whose chain stops parks r and starts the next ID.
+    // Fast steps: every chain busy and >= 64K IDs may still be handed out before the ring
+    // is full or the tile ends; a chain that stops parks r and starts the next ID.
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
-      const uint32_t last = min(len, flushed + kRing) - 64;
+      const uint32_t last = min(len, flushed + kRing) - 2 * kLanes;
       do {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          r = draw(r);
-          const bool stop = chain_stops<RT, Seed>(r, l2m0);
-          if (stop) ring[o & (kRing - 1)] = r;
-          const uint32_t fm = __ballot_sync(kFull, stop);
-          if (stop) {
-            o = hoff + __popc(fm & lt);
-            r = r0 + 2 * static_cast<RT>(o);
+          bool stop[K];
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            r[c] = draw(r[c]);
+            stop[c] = chain_stops<RT, Seed>(r[c], l2m0);
           }
-          hoff += __popc(fm);
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            if (stop[c]) ring[o[c] & (kRing - 1)] = r[c];
+            const uint32_t fm = __ballot_sync(kFull, stop[c]);
+            if (stop[c]) {
+              o[c] = hoff + __popc(fm & lt);
+              r[c] = r0 + 2 * static_cast<RT>(o[c]);
+            }
+            hoff += __popc(fm);
+          }
         }
       } while (hoff <= last);
     };
+    auto in_flight_below = [&](uint32_t edge) {  // any chain of the warp on an edge < edge?
+      bool any = false;
+#pragma unroll
+      for (int c = 0; c < K; ++c) any |= busy[c] && o[c] < edge;
+      return __any_sync(kFull, any);
+    };
 
     for (;;) {
-      if (all_busy && hoff + 64 <= min(len, flushed + kRing)) {
+      if (all_busy && hoff + 2 * kLanes <= min(len, flushed + kRing)) {
         if (HasSeed && l2m0 != 0) fast_loop(std::true_type{});
         else fast_loop(std::false_type{});
       }
       // Make room: write out the oldest chunks whose edges are all done.
-      while (flushed + kChunk <= hoff && !__any_sync(kFull, busy && o < flushed + kChunk)) {
+      while (flushed + kChunk <= hoff && !in_flight_below(flushed + kChunk)) {
         flush(flushed, kChunk);
         flushed += kChunk;
       }
-      if (hoff == len && !__any_sync(kFull, busy)) break;  // tile done
-      // General step: some lanes idle, or the ring or the tile is nearly used up.
-      if (busy) {
-        r = draw(r);
-        if (chain_stops<RT, HasSeed>(r, l2m0)) {
-          ring[o & (kRing - 1)] = r;
-          busy = false;
+      if (hoff == len && !in_flight_below(len)) break;  // tile done
+      // General step: some chains idle, or the ring or the tile is nearly used up.
+      uint32_t room = min(len, flushed + kRing) - hoff;
+      bool idle = false;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        if (busy[c]) {
+          r[c] = draw(r[c]);
+          if (chain_stops<RT, HasSeed>(r[c], l2m0)) {
+            ring[o[c] & (kRing - 1)] = r[c];
+            busy[c] = false;
+          }
         }
+        const uint32_t fm = __ballot_sync(kFull, !busy[c]);
+        const uint32_t k = min(room, static_cast<uint32_t>(__popc(fm)));
+        const uint32_t rank = __popc(fm & lt);
+        if (!busy[c] && rank < k) {
+          o[c] = hoff + rank;
+          r[c] = r0 + 2 * static_cast<RT>(o[c]);
+          busy[c] = true;
+        }
+        hoff += k;
+        room -= k;
+        idle |= !busy[c];
       }
-      const uint32_t fm = __ballot_sync(kFull, !busy);
-      const uint32_t room = min(len, flushed + kRing) - hoff;
-      const uint32_t k = min(room, static_cast<uint32_t>(__popc(fm)));
-      const uint32_t rank = __popc(fm & lt);
-      if (!busy && rank < k) {
-        o = hoff + rank;
-        r = r0 + 2 * static_cast<RT>(o);
-        busy = true;
-      }
-      hoff += k;
-      all_busy = __ballot_sync(kFull, !busy) == 0;
+      all_busy = __ballot_sync(kFull, idle) == 0;
     }
     while (flushed < len) {  // the rest, chunk by chunk (a chunk never wraps the ring)
       const uint32_t c = min(kChunk, len - flushed);
@@ -385,8 +414,9 @@ __device__ __forceinline__ void histogram_add_lane(uint64_t v, unsigned long lon
   else atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
 }
 
-template <class RT, bool HasSeed, class Draw = DrawPlain>
-__global__ void __launch_bounds__(1024)
+// K chains per lane, as in k_generate_refill.
+template <class RT, bool HasSeed, class Draw = DrawPlain, int K = 1>
+__global__ void __launch_bounds__(1024, 1)
 k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64_t node_limit,
                 uint32_t hot, uint64_t *__restrict__ counts) {
   extern __shared__ __align__(16) unsigned long long bins[];
@@ -403,6 +433,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  constexpr uint32_t kLanes = 32u * K;
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
   const bool agg = sp.hist_agg != 0;
@@ -412,7 +443,9 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
                                                              : static_cast<RT>(hit_pos);
 
   // Stopped positions below hp wait in a per-warp ring of kHitRing; once 32 have gathered
-  // the whole warp resolves them together (one target per lane) and counts them.
+  // the whole warp resolves them together (one target per lane) and counts them.  A push
+  // adds at most 32 and the ring is drained below 32 after every push, so it never holds
+  // more than 63.
   RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * kHitRing;
   uint32_t qhead = 0, qtail = 0;  // warp-uniform
   auto drain = [&](uint32_t k) {  // ring entries qhead .. qhead+k-1, k <= 32
@@ -428,6 +461,14 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     qhead += k;
     __syncwarp();
   };
+  auto push = [&](bool hit, RT rv) {  // warp-collective
+    const uint32_t hm = __ballot_sync(kFull, hit);
+    if (hm) {  // most steps have no hit at all
+      if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = rv;
+      qtail += __popc(hm);
+      if (qtail - qhead >= 32) drain(32);
+    }
+  };
 
   for (;;) {  // one tile at a time
     const uint64_t t = next_tile(sp, first, gwarp);
@@ -435,63 +476,72 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     const uint64_t base = g.begin + (t << shift);
     const uint32_t len = static_cast<uint32_t>(min(static_cast<uint64_t>(T), g.end - base));
     const RT r0 = static_cast<RT>(2 * base + 1);
-    uint32_t hoff = min(32u, len);
-    bool busy = static_cast<uint32_t>(lane) < hoff;
-    RT r = r0 + 2 * static_cast<RT>(lane);
-    bool all_busy = hoff == 32;
+    uint32_t hoff = min(kLanes, len);
+    RT r[K];
+    bool busy[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const uint32_t o = 32u * c + lane;
+      busy[c] = o < hoff;
+      r[c] = r0 + 2 * static_cast<RT>(o);
+    }
+    bool all_busy = hoff == kLanes;
 
-    // Fast steps: every lane busy and >= 64 IDs left.  A stopped chain below hp is parked
-    // in the ring, which is drained as soon as 32 entries wait: a step adds at most 32, so
-    // it never holds more than 63.
+    // Fast steps: every chain busy and >= 64K IDs left.
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
-      const uint32_t last = len - 64;
+      const uint32_t last = len - 2 * kLanes;
       do {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          r = draw(r);
-          const bool stop = chain_stops<RT, Seed>(r, two_m0);
-          const bool hit = stop && r < hp;
-          const uint32_t hm = __ballot_sync(kFull, hit);
-          if (hm) {  // most steps have no hit at all
-            if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = r;
-            qtail += __popc(hm);
-            if (qtail - qhead >= 32) drain(32);  // leaves < 32 pending
+          bool stop[K];
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            r[c] = draw(r[c]);
+            stop[c] = chain_stops<RT, Seed>(r[c], two_m0);
           }
-          const uint32_t fm = __ballot_sync(kFull, stop);
-          if (stop) r = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
-          hoff += __popc(fm);
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            push(stop[c] && r[c] < hp, r[c]);
+            const uint32_t fm = __ballot_sync(kFull, stop[c]);
+            if (stop[c]) r[c] = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
+            hoff += __popc(fm);
+          }
         }
       } while (hoff <= last);
     };
 
     for (;;) {
-      if (all_busy && hoff + 64 <= len) {
+      if (all_busy && hoff + 2 * kLanes <= len) {
         if (HasSeed && two_m0 != 0) fast_loop(std::true_type{});
         else fast_loop(std::false_type{});
       }
-      if (hoff == len && !__any_sync(kFull, busy)) break;  // tile done
-      // General step: some lanes idle, or fewer than 64 IDs left.
-      bool stop = false;
-      if (busy) {
-        r = draw(r);
-        stop = chain_stops<RT, HasSeed>(r, two_m0);
+      bool any_busy = false;
+#pragma unroll
+      for (int c = 0; c < K; ++c) any_busy |= busy[c];
+      if (hoff == len && !__any_sync(kFull, any_busy)) break;  // tile done
+      // General step: some chains idle, or fewer than 64K IDs left.
+      bool idle = false;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        bool stop = false;
+        if (busy[c]) {
+          r[c] = draw(r[c]);
+          stop = chain_stops<RT, HasSeed>(r[c], two_m0);
+        }
+        push(stop && r[c] < hp, r[c]);
+        if (stop) busy[c] = false;
+        const uint32_t fm = __ballot_sync(kFull, !busy[c]);
+        const uint32_t k = min(len - hoff, static_cast<uint32_t>(__popc(fm)));
+        const uint32_t rank = __popc(fm & lt);
+        if (!busy[c] && rank < k) {
+          r[c] = r0 + 2 * static_cast<RT>(hoff + rank);
+          busy[c] = true;
+        }
+        hoff += k;
+        idle |= !busy[c];
       }
-      const bool hit = stop && r < hp;
-      const uint32_t hm = __ballot_sync(kFull, hit);
-      if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = r;
-      qtail += __popc(hm);
-      while (qtail - qhead >= 32) drain(32);
-      if (stop) busy = false;
-      const uint32_t fm = __ballot_sync(kFull, !busy);
-      const uint32_t k = min(len - hoff, static_cast<uint32_t>(__popc(fm)));
-      const uint32_t rank = __popc(fm & lt);
-      if (!busy && rank < k) {
-        r = r0 + 2 * static_cast<RT>(hoff + rank);
-        busy = true;
-      }
-      hoff += k;
-      all_busy = __ballot_sync(kFull, !busy) == 0;
+      all_busy = __ballot_sync(kFull, idle) == 0;
     }
   }
   while (qtail != qhead) drain(min(32u, qtail - qhead));
@@ -561,7 +611,8 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
                       (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
-  auto kernel = k_generate_refill<RT, HasSeed, false, Narrow, Draw>;
+  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, false, Narrow, Draw, 2>
+                              : k_generate_refill<RT, HasSeed, false, Narrow, Draw, 1>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   // Tiles of the tuned size, halved (down to 256) until every warp of a full grid has
@@ -606,7 +657,8 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
                       static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit rings
                       (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
-  auto kernel = k_degree_refill<RT, HasSeed, Draw>;
+  auto kernel = s.chains == 2 ? k_degree_refill<RT, HasSeed, Draw, 2>
+                              : k_degree_refill<RT, HasSeed, Draw, 1>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   int grid = 0;
@@ -636,7 +688,8 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
                       static_cast<size_t>(warps) * sizeof(GraphDev);
-  auto kernel = k_generate_refill<RT, HasSeed, true>;
+  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, true, false, DrawPlain, 2>
+                              : k_generate_refill<RT, HasSeed, true, false, DrawPlain, 1>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   SchedParams sp{};

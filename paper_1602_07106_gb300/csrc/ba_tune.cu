@@ -36,10 +36,12 @@ Shape default_shape(int kind) {
   Shape s;
   switch (kind) {
     case BA_KIND_DEGREE:
-      s.block = 512; s.ctas_per_sm = 2; s.tile = 65536; s.refill = 1; s.hist_bins = 12288;
+      s.block = 512; s.ctas_per_sm = 2; s.tile = 16384; s.refill = 1; s.hist_bins = 8192;
+      s.chains = 2;
       break;
     default:  // generate and batch
       s.block = 256; s.ctas_per_sm = 4; s.tile = 16384; s.refill = 1; s.hist_bins = 0;
+      s.chains = 2;
       break;
   }
   return s;
@@ -53,6 +55,7 @@ Shape from_public(const ba_tuning &t, int kind) {
   s.refill = t.refill;
   if (t.hist_bins > 0) s.hist_bins = t.hist_bins;
   s.hist_agg = t.hist_agg;
+  if (t.chains > 0) s.chains = t.chains;
   return s;
 }
 
@@ -64,6 +67,7 @@ void to_public(const Shape &s, ba_tuning *t) {
   t->refill = s.refill;
   t->hist_bins = s.hist_bins;
   t->hist_agg = s.hist_agg;
+  t->chains = s.chains;
 }
 
 bool valid_shape(const Shape &s, int kind) {
@@ -75,6 +79,7 @@ bool valid_shape(const Shape &s, int kind) {
   }
   if (s.hist_bins < 0 || s.hist_bins > 28 * 1024) return false;
   if (s.hist_agg != 0 && s.hist_agg != 1) return false;
+  if (s.chains != 1 && s.chains != 2) return false;
   return true;
 }
 
@@ -90,17 +95,20 @@ ba_status load_file(const char *path, Cache &c) {
   while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
   std::fclose(f);
   // Entries are flat objects {"kind":K,"r32":P,"block":B,"ctas_per_sm":C,"tile":T,
-  // "refill":R,"hist_bins":H}; keys are read in that fixed order.
+  // "refill":R,"hist_bins":H,"hist_agg":A[,"chains":N]}; keys are read in that fixed order
+  // (files without "chains" mean one chain per lane).
   size_t pos = 0;
   int loaded = 0;
   while ((pos = text.find("{\"kind\"", pos)) != std::string::npos) {
     int kind, r32;
     Shape s;
-    if (std::sscanf(text.c_str() + pos,
-                    "{\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-                    "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d}",
-                    &kind, &r32, &s.block, &s.ctas_per_sm, &s.tile, &s.refill, &s.hist_bins,
-                    &s.hist_agg) == 8 &&
+    const int fields = std::sscanf(
+        text.c_str() + pos,
+        "{\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
+        "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d}",
+        &kind, &r32, &s.block, &s.ctas_per_sm, &s.tile, &s.refill, &s.hist_bins, &s.hist_agg,
+        &s.chains);
+    if ((fields == 8 || fields == 9) &&
         kind >= 0 && kind < kKinds && (r32 == 0 || r32 == 1) && valid_shape(s, kind)) {
       c.tuned[kind][r32] = s;
       c.has_tuned[kind][r32] = true;
@@ -145,7 +153,7 @@ ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out) {
   Shape s = from_public(*t, kind);
   if (!valid_shape(s, kind)) {
     set_error("invalid launch shape (block multiple of 32 <= 1024, tile power of two 64..2^20, "
-              "refill 0 or 1, hist_bins <= 28672, hist_agg 0 or 1)");
+              "refill 0 or 1, hist_bins <= 28672, hist_agg 0 or 1, chains 1 or 2)");
     return BA_ERR_INVALID_ARG;
   }
   *out = s;
@@ -200,15 +208,16 @@ std::vector<Shape> candidates(int kind) {
     const int bins[] = {4096, 8192, 12288, 24576};
     for (int blk : dblocks)
       for (int ctas : {1, 2, 4})
-        for (int tile : tiles)
+        for (int tile : {16384, 65536})
           for (int hb : bins) {
             if (blk * ctas > 2048 || static_cast<size_t>(hb) * 8 * ctas > 220 * 1024) continue;
-            for (int agg : {0, 1}) {
-              Shape s;
-              s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1; s.hist_bins = hb;
-              s.hist_agg = agg;
-              out.push_back(s);
-            }
+            for (int agg : {0, 1})
+              for (int chains : {1, 2}) {
+                Shape s;
+                s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1;
+                s.hist_bins = hb; s.hist_agg = agg; s.chains = chains;
+                out.push_back(s);
+              }
           }
     Shape simple;
     simple.block = 256; simple.ctas_per_sm = 8; simple.tile = 512; simple.refill = 0;
@@ -217,12 +226,13 @@ std::vector<Shape> candidates(int kind) {
   }
   for (int blk : blocks)
     for (int ctas : {2, 4, 8})
-      for (int tile : tiles) {
-        if (blk * ctas > 2048) continue;
-        Shape s;
-        s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1;
-        out.push_back(s);
-      }
+      for (int tile : tiles)
+        for (int chains : {1, 2}) {
+          if (blk * ctas > 2048) continue;
+          Shape s;
+          s.block = blk; s.ctas_per_sm = ctas; s.tile = tile; s.refill = 1; s.chains = chains;
+          out.push_back(s);
+        }
   if (kind == BA_KIND_GENERATE) {
     Shape simple;
     simple.block = 256; simple.ctas_per_sm = 8; simple.tile = 512; simple.refill = 0;
@@ -384,9 +394,9 @@ ba_status ba_tune_save(const char *path) {
       const Shape &s = c.tuned[k][r];
       std::fprintf(f,
                    "%s\n  {\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-                   "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d}",
+                   "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d}",
                    firstw ? "" : ",", k, r, s.block, s.ctas_per_sm, s.tile, s.refill, s.hist_bins,
-                   s.hist_agg);
+                   s.hist_agg, s.chains);
       firstw = false;
     }
   std::fprintf(f, "\n]}\n");

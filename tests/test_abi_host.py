@@ -99,7 +99,8 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
     default = ba.ba_get_tuning(ba.BA_KIND_GENERATE)
     assert default["block"] % 32 == 0 and default["tile"] & (default["tile"] - 1) == 0
     for bad in ({"block": 100, "refill": 1}, {"tile": 100, "refill": 1}, {"refill": 3},
-                {"block": 2048, "refill": 1}, {"refill": 1, "hist_agg": 2}):
+                {"block": 2048, "refill": 1}, {"refill": 1, "hist_agg": 2},
+                {"refill": 1, "chains": 3}):
         with pytest.raises(ba.BAError):
             ba.ba_set_tuning(ba.BA_KIND_GENERATE, bad)
     ba.ba_set_tuning(ba.BA_KIND_GENERATE, {"block": 128, "ctas_per_sm": 8, "tile": 1024,
@@ -113,9 +114,13 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
     ba.ba_tune_load(str(path))
     assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["hist_bins"] == 8192
     assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["hist_agg"] == 1
+    assert ba.ba_get_tuning(ba.BA_KIND_DEGREE, 2**40)["chains"] == 1   # entry without "chains"
     out = tmp_path / "saved.json"
     ba.ba_tune_save(str(out))
-    assert '"hist_bins": 8192' in out.read_text()
+    assert '"hist_bins": 8192' in out.read_text() and '"chains": 1' in out.read_text()
+    ba.ba_set_tuning(ba.BA_KIND_GENERATE, {"refill": 1, "chains": 2})
+    assert ba.ba_get_tuning(ba.BA_KIND_GENERATE)["chains"] == 2
+    ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
     with pytest.raises(ba.BAError):
         ba.ba_tune_load(str(tmp_path / "missing.json"))
 

@@ -74,7 +74,9 @@ def test_batch_ranges_gaps_and_64_bit_graphs_equal_plain_calls(ba):
 
 
 @pytest.mark.parametrize("shape", [{"refill": 1, "block": 64, "ctas_per_sm": 2, "tile": 64},
-                                   {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 1024}])
+                                   {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 1024},
+                                   {"refill": 1, "block": 256, "ctas_per_sm": 4, "tile": 256,
+                                    "chains": 2}])
 def test_batch_output_does_not_depend_on_shape(ba, shape):
     table = W.batch_table(G=64, n_lo=1e2, n_hi=1e4, table_seed=3)
     graphs = [(g.seed, g.n, g.d, g.n0, 0, g.m) for g in table]

@@ -56,6 +56,9 @@ SHAPES = [
     {"refill": 1, "block": 128, "ctas_per_sm": 8, "tile": 256, "hist_bins": 64, "hist_agg": 1},
     {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 1024, "hist_bins": 26624},
     {"refill": 1, "block": 32, "ctas_per_sm": 4, "tile": 4096, "hist_bins": 7},
+    {"refill": 1, "block": 256, "ctas_per_sm": 2, "tile": 512, "hist_bins": 4096, "chains": 2},
+    {"refill": 1, "block": 512, "ctas_per_sm": 1, "tile": 16384, "hist_bins": 8192, "hist_agg": 1,
+     "chains": 2},
 ]
 
 
@@ -98,13 +101,15 @@ def test_large_workload_prefix_partition_and_degree_sum(ba):
 
 
 def test_streaming_workload_prefix_and_partition(ba):
-    # n = 10^10, d = 100: the section 3 experiment scaled 1000x down.  The oracle checks a
-    # 10^8-edge prefix; the full 10^12-edge count is checked for split invariance.
+    # n = 10^10, d = 100: the section 3 experiment scaled 1000x down.  The oracle checks the
+    # 10^9-edge prefix and the last 10^8 edges (64-bit positions); the full 10^12-edge count
+    # is checked for split invariance.
     g = W.STREAM_HUGE
     L = W.DEGREE_NODE_LIMIT
-    a = 10**8
-    np.testing.assert_array_equal(_counts(ba, g.seed, g.n, g.d, 0, 0, a, L).cpu().numpy().astype(np.uint64),
-                                  opar.degree_count_range(g.seed, g.n, g.d, 0, 0, a, L))
+    for a, b in [(0, 10**9), (g.m - 10**8, g.m)]:
+        np.testing.assert_array_equal(
+            _counts(ba, g.seed, g.n, g.d, 0, a, b, L).cpu().numpy().astype(np.uint64),
+            opar.degree_count_range(g.seed, g.n, g.d, 0, a, b, L))
     full = torch.empty(L, dtype=torch.int64, device="cuda")
     ba.ba_degree_count(g.seed, g.n, g.d, L, full)
     cut = 5 * 10**11 + 3

@@ -67,6 +67,10 @@ SHAPES = [
     {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 1024},
     {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 512},
     {"refill": 1, "block": 64, "ctas_per_sm": 16, "tile": 4096},
+    {"refill": 1, "block": 32, "ctas_per_sm": 1, "tile": 64, "chains": 2},
+    {"refill": 1, "block": 128, "ctas_per_sm": 2, "tile": 128, "chains": 2},
+    {"refill": 1, "block": 256, "ctas_per_sm": 4, "tile": 16384, "chains": 2},
+    {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 2048, "chains": 2},
 ]
 
 

@@ -33,7 +33,9 @@ def test_int32_edges_match_oracle(ba, seed, n, d, n0, a, b):
 
 @pytest.mark.parametrize("shape", [{"refill": 0, "block": 256, "ctas_per_sm": 8},
                                    {"refill": 1, "block": 64, "ctas_per_sm": 8, "tile": 64},
-                                   {"refill": 1, "block": 256, "ctas_per_sm": 1, "tile": 2048}])
+                                   {"refill": 1, "block": 256, "ctas_per_sm": 1, "tile": 2048},
+                                   {"refill": 1, "block": 128, "ctas_per_sm": 2, "tile": 256,
+                                    "chains": 2}])
 def test_int32_output_does_not_depend_on_shape(ba, shape):
     try:
         ba.ba_set_tuning(ba.BA_KIND_GENERATE, shape)

@@ -73,7 +73,8 @@ def test_variant_zero_is_the_plain_graph(ba):
     {"refill": 1, "block": 32, "ctas_per_sm": 1, "tile": 64},
     {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 2048},
     {"refill": 0, "block": 256, "ctas_per_sm": 4},            # variants still use refill
-], ids=["b32-t64", "b1024-t2048", "simple"])
+    {"refill": 1, "block": 256, "ctas_per_sm": 2, "tile": 1024, "chains": 2},
+], ids=["b32-t64", "b1024-t2048", "simple", "b256-t1024-c2"])
 def test_output_does_not_depend_on_launch_shape(ba, shape):
     seed, n, d, n0, a, b = 31, 200_000, 3, 4, 5, 599_994
     want = {v: _oracle(seed, n, d, n0, a, b, v) for v in VARIANTS}
