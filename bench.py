@@ -536,13 +536,26 @@ def extras(args, ba, torch, stream, main):
         ts = _time_events(lambda: ba.ba_batch_plan_launch(plan, out_b, stream), stream, torch, 5)
     finally:
         ba.ba_batch_plan_destroy(plan)
+    # the same graphs through one plain call each, into the same packed buffer
+    offs = [0]
+    for gr in graphs:
+        offs.append(offs[-1] + gr[5] - gr[4])
+
+    def plain_calls():
+        for k, (sd, nn, dd, n0, a, b) in enumerate(graphs):
+            ba.ba_generate_edges(sd, nn, dd, n0, a, b, out_b[offs[k]:offs[k + 1]], stream)
+
+    plain_calls()
+    tp = _time_events(plain_calls, stream, torch, 3)
     plain_rate = 2**31 / (main["kernels_ms"]["generate"] / 1e3)
     ex["batched"] = {"workload": f"{len(graphs)} graphs of the 4096-graph table (seed 1000+g, "
                                  f"n log-uniform 1e3..1e7, d 1..32, half clique seeds), "
                                  f"{total} edges in one persistent launch (CUDA graph replay)",
                      "graphs": len(graphs), "edges": total,
                      "edges_per_s": total / statistics.median(ts),
-                     "vs_plain": (total / statistics.median(ts)) / plain_rate}
+                     "vs_plain": (total / statistics.median(ts)) / plain_rate,
+                     "plain_calls_same_graphs_edges_per_s": total / statistics.median(tp),
+                     "vs_plain_calls_same_graphs": statistics.median(tp) / statistics.median(ts)}
     del out_b
     torch.cuda.empty_cache()
     ex["variants"] = variants(ba, torch, stream, main)
