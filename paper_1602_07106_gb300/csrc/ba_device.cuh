@@ -112,7 +112,9 @@ __device__ __forceinline__ uint32_t div32(uint32_t x, const FastDiv &f) {
 // E[2k] = v, E[2k+1] = u.  v comes from the quadratic formula, corrected to the exact
 // integer by the two loops.  The estimate uses single precision (fast on every SM; off by
 // at most a few steps below 2^40) and double precision only for larger seed cliques.
-__device__ __forceinline__ uint64_t clique_position(uint64_t p) {
+// Out of line: it runs for a few in 10^4 edges, and inlined copies in every kernel's flush
+// and count paths slowed the common path of seeded graphs by ~10 % (code size).
+static __device__ __noinline__ uint64_t clique_position(uint64_t p) {
   if (p < (1ull << 31)) {  // 32-bit fast path: k < 2^30, so v <= 46341 and v(v+1) < 2^32
     const uint32_t k = static_cast<uint32_t>(p >> 1);
     uint32_t v = static_cast<uint32_t>((1.0f + sqrtf(8.0f * static_cast<float>(k) + 1.0f)) * 0.5f);

@@ -125,7 +125,6 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         else
           __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       };
-      [[maybe_unused]] bool seed_seen = false;
       if (!HasSeed && n0 == 0) {
         // Empty seed graph: source i/d, target (r/2)/d; with d = 2^l both are one shift.
         const uint32_t l1 = dv.l + 1;
@@ -136,26 +135,36 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
           else put(j, div(b32 + j), div(r >> 1));
         }
       } else {
+        // A chain that stopped inside the seed names a clique node (a few in 10^4 chains:
+        // the seed nodes' share of all end points).  Bit k of `fix` marks the lane's k-th
+        // edge of the chunk as one; those few pairs are rewritten afterwards.
+        [[maybe_unused]] uint32_t fix = 0;
+        uint32_t bit = 1;
 #pragma unroll 4
-        for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+        for (uint32_t j = threadIdx.x & 31; j < len; j += 32, bit <<= 1) {
           const uint32_t i = b32 + j;
           const uint32_t r = stage[j];
-          if constexpr (HasSeed) seed_seen |= r < two_m0;
+          if constexpr (HasSeed) fix |= r < two_m0 ? bit : 0u;
           put(j, n0 + div(i - m0), n0 + div((r >> 1) - m0));
+        }
+        if constexpr (HasSeed) {
+          if (__any_sync(kFull, fix != 0)) {
+            while (fix) {  // by the lane that wrote the pair
+              const uint32_t j = (threadIdx.x & 31) + 32u * (__ffs(fix) - 1);
+              fix &= fix - 1;
+              put(j, n0 + div(b32 + j - m0), static_cast<uint32_t>(clique_position(stage[j])));
+            }
+          }
         }
       }
       if constexpr (HasSeed) {
-        // Seed edges (the first m0 of the graph) and chains that stopped inside the seed
-        // are rare: a second pass over the chunk rewrites just those pairs.
-        if (__any_sync(kFull, seed_seen) || b32 < seed_m0) {
+        // The seed edges themselves (the graph's first m0) sit in its first chunks only.
+        if (b32 < seed_m0) {
           for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
             const uint32_t i = b32 + j;
-            const uint32_t r = stage[j];
             if (i < seed_m0)
               put(j, static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i))),
                   static_cast<uint32_t>(clique_position(2 * static_cast<uint64_t>(i) + 1)));
-            else if (r < two_m0)
-              put(j, n0 + div(i - m0), static_cast<uint32_t>(clique_position(r)));
           }
         }
       }
