@@ -123,3 +123,14 @@ def test_streaming_workload_prefix_and_partition(ba):
     ys = [np.log(c[x:y].mean()) for x, y in zip(cuts[:-1], cuts[1:])]
     slope = np.polyfit(xs, ys, 1)[0]
     assert -0.55 <= slope <= -0.45      # Fig. 2: degree ~ d sqrt(n/j)
+
+
+@pytest.mark.parametrize("seed,n,d,n0", [(5, 100_500, 3, 100_000), (6, 2**20 + 13, 2, 2**20 + 3)])
+def test_huge_seed_cliques(ba, seed, n, d, n0):
+    # closed-form clique end points (k_degree_init) and chains that stop in a clique whose
+    # positions exceed 2^32 (and 2^40)
+    m0 = n0 * (n0 - 1) // 2
+    m = ba.ba_num_edges(n, d, n0)
+    for a, b, limit in [(m0 - 700, m, n), (m0 - 700, m, 5000), (0, 500, 40)]:
+        np.testing.assert_array_equal(_counts(ba, seed, n, d, n0, a, b, limit).cpu().numpy().astype(np.uint64),
+                                      oracle.degree_count_range(seed, n, d, n0, a, b, limit))

@@ -128,3 +128,14 @@ def test_large_workload_full_size_spot_ranges_and_properties(ba):
         assert bool((blk[:, 1] <= blk[:, 0]).all()) and bool((blk[:, 1] >= 0).all())
     del out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("seed,n,d,n0", [(5, 100_500, 3, 100_000),        # m0 ~ 5e9: 64-bit positions
+                                         (6, 2**20 + 13, 2, 2**20 + 3)])  # 2 m0 > 2^40
+def test_huge_seed_cliques(ba, seed, n, d, n0):
+    # the clique lookup's float estimate (and, above 2^40, double) on positions beyond 2^32
+    m0 = n0 * (n0 - 1) // 2
+    m = ba.ba_num_edges(n, d, n0)
+    for a, b in [(m0 - 700, min(m, m0 + 700)), (max(m0 - 300, m - 700), m), (0, 300)]:
+        np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
+                                      oracle.edges_range(seed, n, d, n0, a, b))
