@@ -426,15 +426,11 @@ def gpu_arm(args):
             pinned = False
         host_counts = torch.empty(NODE_LIMIT, dtype=torch.int64, pin_memory=pinned)
 
-        side = torch.cuda.Stream()
-
         def e2e_step():
-            # the degree count runs on a second stream while the edge list streams to the
-            # host (that copy, not the GPU, bounds this step)
-            side.wait_stream(stream)
-            ba.ba_degree_count_range(g.seed, n_total, g.d, 0, a0, a1, NODE_LIMIT, counts, 0, side)
+            # (a second stream for the degree count was measured: its persistent grid
+            # delays the chunks that feed the host copy, so the step got slower)
             ba.ba_generate_edges_host(g.seed, n_total, g.d, 0, a0, a1, host_out, stream)
-            stream.wait_stream(side)
+            ba.ba_degree_count_range(g.seed, n_total, g.d, 0, a0, a1, NODE_LIMIT, counts, 0, stream)
             if world > 1:
                 shard.sum_degree_counts(counts)
             host_counts.copy_(counts, non_blocking=True)
