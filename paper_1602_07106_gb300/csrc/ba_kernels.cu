@@ -115,9 +115,11 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     // d a power of two (d = 2^l): the divisions are shifts.
     auto body = [&](auto pow2_tag) {
       constexpr bool Pow2 = decltype(pow2_tag)::value;
+      // d not a power of two: d >= 3, so l >= 2 and the multiply-high path always applies
+      const uint32_t np2_shift = dv.l - 1;
       auto div = [&](uint32_t x) -> uint32_t {
         if constexpr (Pow2) return x >> dv.l;
-        else return div32(x, dv);
+        else return __umulhi(x, dv.m32) >> np2_shift;
       };
       auto put = [&](uint32_t j, uint32_t u, uint32_t v) {
         if constexpr (Narrow)
