@@ -246,9 +246,21 @@ def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
         pool.map(opar._edges_piece, jobs_e)
         pool.map(opar._degrees_piece, jobs_d)
         dt = time.perf_counter() - t0
+    # single core, the paper's comparison (section 3): the Batagelj-Brandes array against
+    # the recomputation of Fig. 1, on the small workload
+    sm = W.PLAIN_SMALL
+    t0 = time.perf_counter()
+    oracle.bb_array(sm.seed, sm.n, sm.d, 0)
+    t_bb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.edges_range(sm.seed, sm.n, sm.d, 0, 0, sm.m)
+    t_rc = time.perf_counter() - t0
     return {"value": 2 * sample_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
             "sample": f"edges [0, {sample_edges}) of n=2^27 d=16 seed=42: edge list + degree "
-                      f"count of nodes < 1e5, {dt:.1f} s wall on {cores} processes"}
+                      f"count of nodes < 1e5, {dt:.1f} s wall on {cores} processes",
+            "one_core_small_workload": {
+                "workload": "n=1e6 d=4 seed=1, 4e6 edges",
+                "bb_array_edges_per_s": sm.m / t_bb, "recompute_edges_per_s": sm.m / t_rc}}
 
 
 # ---------------------------------------------------------------------- GPU arm --
