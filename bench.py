@@ -35,6 +35,8 @@ from paper_1602_07106_gb300 import shard  # noqa: E402
 from paper_1602_07106_gb300 import workloads as W  # noqa: E402
 
 NODE_LIMIT = W.DEGREE_NODE_LIMIT
+WORKLOAD = ("plain BA n=2^27 d=16 seed=42, m=2^31 edges per GPU (edge list 34.4 GB in HBM + "
+            "degree count of nodes < 1e5)")
 FALLBACK_HBM_GBS = 6800.0
 SM_COUNT_NOMINAL = 152
 SMSP_PER_SM = 4
@@ -219,8 +221,10 @@ def reference_arm(args):
         "value": value, "unit": "edges/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "plain BA n=2^27 d=16 seed=42 (sampled)",
-                   "sample_edges_per_step": 2 * sample},
+        "config": {"workload": WORKLOAD,
+                   "sample": f"each step: edges [0, {sample}) of that graph, generated and "
+                             f"degree-counted (2 x {sample} edge generations)",
+                   "parallelism": f"{cores} host processes"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
                          "sample": f"edges [0, {sample}) generated and degree-counted per step"},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -415,8 +419,7 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": "plain BA n=2^27 d=16 seed=42, m=2^31 edges per GPU "
-                               "(edge list 34.4 GB in HBM + degree count of nodes < 1e5)",
+        "config": {"workload": WORKLOAD,
                    "edges_per_step": edges_per_step, "l2": "working set 34.4 GB > L2, no flush",
                    "parallelism": f"edge-range shards x{world}",
                    "tuning": tuned or "library defaults"},
