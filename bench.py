@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-sample-edges", type=int, default=2**28)
-    ap.add_argument("--profile", choices=["generate", "degree", "batch"], default=None,
+    ap.add_argument("--profile", choices=["generate", "degree", "batch", "degree64", "crc"],
+                    default=None,
                     help="run a small case of one kernel (for ncu captures) and exit")
     ap.add_argument("--profile-edges", type=int, default=2**26)
     ap.add_argument("--profile-reps", type=int, default=3)
@@ -77,6 +78,18 @@ def profile_case(args):
         out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
         for _ in range(args.profile_reps):
             ba.ba_generate_edges(g.seed, g.n, g.d, 0, 0, e, out, stream)
+    elif args.profile == "degree64":
+        # the streaming workload (n = 1e10, d = 100): 64-bit positions, from mid-graph
+        h = W.STREAM_HUGE
+        counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+        a = h.m // 2
+        for _ in range(args.profile_reps):
+            ba.ba_degree_count_range(h.seed, h.n, h.d, 0, a, a + e, NODE_LIMIT, counts, 0, stream)
+    elif args.profile == "crc":
+        out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
+        for _ in range(args.profile_reps):
+            ba.ba_generate_edges_variant(g.seed, g.n, g.d, 0, 0, e, ba.BA_VARIANT_CRC_HASH, out,
+                                         stream)
     elif args.profile == "degree":
         # a slice from the middle of the graph: its share of targets below 1e5 (~2%) is
         # that of the whole graph, unlike a prefix
