@@ -92,9 +92,9 @@ __device__ __forceinline__ void copy_graph(GraphDev *dst, const GraphDev *src) {
   __syncwarp();
 }
 
-// Writes the finished tile [base, base+len) of one slot: lane j of the warp handles
-// edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes (256 with
-// Narrow int32 pairs).
+// Writes the finished chunk [base, base+len) of the staging ring: lane j of the warp
+// handles edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes (256
+// with Narrow int32 pairs).
 template <class RT, bool HasSeed, bool Narrow = false>
 __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint32_t len,
                                            const GraphDev &g, int64_t *__restrict__ out) {
