@@ -415,7 +415,7 @@ __device__ __forceinline__ void histogram_add(bool hit, uint64_t v, unsigned lon
 }
 
 // Entries of the per-warp ring of stopped positions that may hit a counted node.
-constexpr uint32_t kHitRing = 128;
+constexpr uint32_t kHitRing = 256;
 
 // One end point at node v from the calling lane alone: a shared-memory bin below `hot`,
 // else the global counter.
@@ -445,6 +445,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kLanes = 32u * K;
+  static_assert(31 + 2 * kLanes <= kHitRing, "two steps' hits must fit in the hit ring");
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
   const bool agg = sp.hist_agg != 0;
@@ -454,9 +455,8 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
                                                              : static_cast<RT>(hit_pos);
 
   // Stopped positions below hp wait in a per-warp ring of kHitRing; once 32 have gathered
-  // the whole warp resolves them together (one target per lane) and counts them.  A push
-  // adds at most 32 and the ring is drained below 32 after every push, so it never holds
-  // more than 63.
+  // the whole warp resolves them together (one target per lane) and counts them.  The ring
+  // is drained below 32 after every general-step push and after every two fast steps.
   RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * kHitRing;
   uint32_t qhead = 0, qtail = 0;  // warp-uniform
   auto drain = [&](uint32_t k) {  // ring entries qhead .. qhead+k-1, k <= 32
@@ -479,6 +479,13 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
       qtail += __popc(hm);
       if (qtail - qhead >= 32) drain(32);
     }
+  };
+  // The fast steps' form: no branch per step (the pushes are predicated stores), the ring
+  // is drained after every two steps, which add at most 64K entries to < 32 waiting.
+  auto push_nobranch = [&](bool hit, RT rv) {  // warp-collective
+    const uint32_t hm = __ballot_sync(kFull, hit);
+    if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = rv;
+    qtail += __popc(hm);
   };
 
   for (;;) {  // one tile at a time
@@ -513,12 +520,13 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
           }
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            push(stop[c] && r[c] < hp, r[c]);
+            push_nobranch(stop[c] && r[c] < hp, r[c]);
             const uint32_t fm = __ballot_sync(kFull, stop[c]);
             if (stop[c]) r[c] = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
             hoff += __popc(fm);
           }
         }
+        while (qtail - qhead >= 32) drain(32);
       } while (hoff <= last);
     };
 
