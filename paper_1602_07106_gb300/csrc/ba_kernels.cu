@@ -415,7 +415,7 @@ __device__ __forceinline__ void histogram_add(bool hit, uint64_t v, unsigned lon
 }
 
 // Entries of the per-warp ring of stopped positions that may hit a counted node.
-constexpr uint32_t kHitRing = 256;
+constexpr uint32_t kHitRing = 512;
 
 // One end point at node v from the calling lane alone: a shared-memory bin below `hot`,
 // else the global counter.
@@ -445,7 +445,8 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kLanes = 32u * K;
-  static_assert(31 + 2 * kLanes <= kHitRing, "two steps' hits must fit in the hit ring");
+  constexpr uint32_t kSteps = 4;  // fast steps between bounds checks and ring drains
+  static_assert(31 + kSteps * kLanes <= kHitRing, "a fast iteration's hits must fit in the hit ring");
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
   const bool agg = sp.hist_agg != 0;
@@ -508,10 +509,10 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     // Fast steps: every chain busy and >= 64K IDs left.
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
-      const uint32_t last = len - 2 * kLanes;
+      const uint32_t last = len - kSteps * kLanes;
       do {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kSteps; ++u) {
           bool stop[K];
 #pragma unroll
           for (int c = 0; c < K; ++c) {
@@ -531,7 +532,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     };
 
     for (;;) {
-      if (all_busy && hoff + 2 * kLanes <= len) {
+      if (all_busy && hoff + kSteps * kLanes <= len) {
         if (HasSeed && two_m0 != 0) fast_loop(std::true_type{});
         else fast_loop(std::false_type{});
       }

@@ -54,7 +54,7 @@ SHAPES = [
     {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 512, "hist_bins": 1000},
     {"refill": 1, "block": 512, "ctas_per_sm": 2, "tile": 512, "hist_bins": 24576, "hist_agg": 1},
     {"refill": 1, "block": 128, "ctas_per_sm": 8, "tile": 256, "hist_bins": 64, "hist_agg": 1},
-    {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 1024, "hist_bins": 24576},
+    {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 1024, "hist_bins": 20480},
     {"refill": 1, "block": 32, "ctas_per_sm": 4, "tile": 4096, "hist_bins": 7},
     {"refill": 1, "block": 256, "ctas_per_sm": 2, "tile": 512, "hist_bins": 4096, "chains": 2},
     {"refill": 1, "block": 512, "ctas_per_sm": 1, "tile": 16384, "hist_bins": 8192, "hist_agg": 1,
