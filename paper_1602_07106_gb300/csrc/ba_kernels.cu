@@ -297,10 +297,14 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
         else fast_loop(std::false_type{});
       }
       // Make room: write out the oldest chunks whose edges are all done.
+      bool made_room = false;
       while (flushed + kChunk <= hoff && !in_flight_below(flushed + kChunk)) {
         flush(flushed, kChunk);
         flushed += kChunk;
+        made_room = true;
       }
+      // Every chain still busy and room again: back to the fast steps directly.
+      if (made_room && all_busy && hoff + 2 * kLanes <= min(len, flushed + kRing)) continue;
       if (hoff == len && !in_flight_below(len)) break;  // tile done
       // General step: some chains idle, or the ring or the tile is nearly used up.
       uint32_t room = min(len, flushed + kRing) - hoff;
