@@ -338,15 +338,17 @@ def gpu_arm(args):
     out = torch.empty((m_shard, 2), dtype=torch.int64, device="cuda")
     counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
 
-    # The library's autotuner picks each kernel's launch shape on a 2^29-edge sample of this
-    # rank's range (outside the timed region); the output never depends on the shape.
+    # The library's autotuner picks each kernel's launch shape outside the timed region; the
+    # output never depends on the shape.  The step's two kernels are tuned on this rank's
+    # whole range (shorter samples shrink the tiles, so tile sizes that differ at full size
+    # would look alike); the batched kernel, which serves small chunks too, and the 64-bit
+    # degree path on a 2^29-edge sample.
     tuned = {}
     if not args.no_tune:
         smp = min(2**29, m_shard)
-        mid = a0 + m_shard // 2
-        tuned["generate"] = ba.ba_tune(ba.BA_KIND_GENERATE, g.seed, n_total, g.d, 0, a1 - smp, a1,
+        tuned["generate"] = ba.ba_tune(ba.BA_KIND_GENERATE, g.seed, n_total, g.d, 0, a0, a1,
                                        out, stream)
-        tuned["degree"] = ba.ba_tune(ba.BA_KIND_DEGREE, g.seed, n_total, g.d, 0, mid, mid + smp,
+        tuned["degree"] = ba.ba_tune(ba.BA_KIND_DEGREE, g.seed, n_total, g.d, 0, a0, a1,
                                      None, stream)
         tuned["batch"] = ba.ba_tune(ba.BA_KIND_BATCH, g.seed, n_total, g.d, 0, a1 - smp, a1, out,
                                     stream)

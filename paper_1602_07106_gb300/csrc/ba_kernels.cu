@@ -449,7 +449,9 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kLanes = 32u * K;
-  constexpr uint32_t kSteps = 4;  // fast steps between bounds checks and ring drains
+  // Fast steps between bounds checks and ring drains: 4 on the 32-bit path; the 64-bit
+  // path's longer hash runs out of registers with 4 (measured slower) and takes 2.
+  constexpr uint32_t kSteps = sizeof(RT) == 4 ? 4 : 2;
   static_assert(31 + kSteps * kLanes <= kHitRing, "a fast iteration's hits must fit in the hit ring");
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
@@ -525,7 +527,10 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
           }
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            push_nobranch(stop[c] && r[c] < hp, r[c]);
+            // 32-bit path: predicated pushes; 64-bit path: one uniform branch (measured
+            // faster there)
+            if constexpr (sizeof(RT) == 4) push_nobranch(stop[c] && r[c] < hp, r[c]);
+            else push(stop[c] && r[c] < hp, r[c]);
             const uint32_t fm = __ballot_sync(kFull, stop[c]);
             if (stop[c]) r[c] = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
             hoff += __popc(fm);
