@@ -139,3 +139,33 @@ def test_huge_seed_cliques(ba, seed, n, d, n0):
     for a, b in [(m0 - 700, min(m, m0 + 700)), (max(m0 - 300, m - 700), m), (0, 300)]:
         np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
                                       oracle.edges_range(seed, n, d, n0, a, b))
+
+
+def test_concurrent_calls_from_host_threads(ba):
+    # the library is called from several host threads at once, each on its own stream
+    # (ctypes releases the GIL): every result is the one a lone call gives
+    import threading
+    cases = [(101 + k, 50_000 + 1000 * k, 1 + k % 5, (k % 3) * 4) for k in range(8)]
+    want = {c: oracle.bb_array(*c).reshape(-1, 2) for c in cases}
+    got, errors = {}, []
+
+    def worker(c):
+        try:
+            s = torch.cuda.Stream()
+            m = want[c].shape[0]
+            out = torch.empty((m, 2), dtype=torch.int64, device="cuda")
+            for _ in range(3):
+                ba.ba_generate_edges(*c, 0, m, out, s)
+            s.synchronize()
+            got[c] = out.cpu().numpy()
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(c,)) for c in cases]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for c in cases:
+        np.testing.assert_array_equal(got[c], want[c])
