@@ -19,7 +19,10 @@
 
 namespace ba {
 
-struct DrawPlain {
+// Ptx: the 32-bit path uses hash_r32_pre_ptx (same values; faster in the degree kernel).
+template <bool Ptx>
+struct DrawPlainT {
+  static constexpr bool kPlain = true;
   static constexpr bool kTables = false;
   static constexpr bool kNeedsSeed = false;
   uint64_t spre = 0;
@@ -28,8 +31,13 @@ struct DrawPlain {
   // Per tile: the graph whose positions are drawn next.
   __device__ __forceinline__ void bind(const GraphDev &g) { spre = g.seed_pre; }
   template <class RT>
-  __device__ __forceinline__ RT operator()(RT r) const { return hash_pre<RT>(spre, r); }
+  __device__ __forceinline__ RT operator()(RT r) const {
+    if constexpr (Ptx && sizeof(RT) == 4) return hash_r32_pre_ptx(spre, r);
+    else return hash_pre<RT>(spre, r);
+  }
 };
+using DrawPlain = DrawPlainT<false>;
+using DrawPlainPtx = DrawPlainT<true>;
 
 // CRC-32C in bit-reflected form (polynomial 0x1EDC6F41 reversed).
 constexpr uint32_t kCrc32cReflected = 0x82F63B78u;
@@ -66,6 +74,7 @@ __host__ __device__ constexpr size_t crc_table_smem(bool r32) {
 
 template <bool Crc, bool NoLoop>
 struct DrawVariant {
+  static constexpr bool kPlain = false;
   static constexpr bool kTables = Crc;
   static constexpr bool kNeedsSeed = NoLoop;  // the first new node needs a seed edge
   uint64_t spre = 0;            // SplitMix64 draws

@@ -626,7 +626,7 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
                      cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
-  if constexpr (std::is_same_v<Draw, DrawPlain>) {  // the simple kernel draws h(r) only
+  if constexpr (Draw::kPlain) {  // the simple kernel draws h(r) only
     if (s.refill == 0) {
       int grid = 0;
       ba_status st = persistent_grid(k_generate_simple<RT, HasSeed, Narrow>, block, 0,
@@ -671,7 +671,7 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
                    const Shape &s, unsigned long long *counter, cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
-  if constexpr (std::is_same_v<Draw, DrawPlain>) {
+  if constexpr (Draw::kPlain) {
     if (s.refill == 0) {
       int grid = 0;
       ba_status st = persistent_grid(k_degree_simple<RT, HasSeed>, block, 0, s.ctas_per_sm,
@@ -826,7 +826,7 @@ ba_status degree_with(const GraphDev &g_in, uint64_t node_limit, uint64_t *count
 
 ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts, int accumulate,
                         const Shape &s, unsigned long long *counter, cudaStream_t stream) {
-  return degree_with<DrawPlain>(g, node_limit, counts, accumulate, s, counter, stream);
+  return degree_with<DrawPlainPtx>(g, node_limit, counts, accumulate, s, counter, stream);
 }
 
 ba_status launch_generate_variant(const GraphDev &g, int64_t *out, const Shape &s,
@@ -850,7 +850,7 @@ ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t
                                 int accumulate, const Shape &s, unsigned long long *counter,
                                 cudaStream_t stream, uint32_t variant) {
   switch (variant) {
-    case 0: return degree_with<DrawPlain>(g, node_limit, counts, accumulate, s, counter, stream);
+    case 0: return degree_with<DrawPlainPtx>(g, node_limit, counts, accumulate, s, counter, stream);
     case kVariantCrc:
       return degree_with<DrawVariant<true, false>>(g, node_limit, counts, accumulate, s, counter, stream);
     case kVariantNoLoop:
