@@ -130,7 +130,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
       if (!HasSeed && n0 == 0) {
         // Empty seed graph: source i/d, target (r/2)/d; with d = 2^l both are one shift.
         const uint32_t l1 = dv.l + 1;
-#pragma unroll 4
+#pragma unroll 8
         for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
           const uint32_t r = stage[j];
           if constexpr (Pow2) put(j, (b32 + j) >> dv.l, r >> l1);
