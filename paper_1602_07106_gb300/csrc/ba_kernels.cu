@@ -127,7 +127,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         else
           __stcs(dst + j, make_int4(static_cast<int>(u), 0, static_cast<int>(v), 0));
       };
-      if (!HasSeed && n0 == 0) {
+      if (n0 == 0) {  // also the unseeded graphs of a batched launch that has seeded ones
         // Empty seed graph: source i/d, target (r/2)/d; with d = 2^l both are one shift.
         const uint32_t l1 = dv.l + 1;
 #pragma unroll 8
