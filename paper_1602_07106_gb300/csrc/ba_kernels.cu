@@ -173,6 +173,13 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     };
     if (dv.pow2) body(std::true_type{});
     else body(std::false_type{});
+  } else if (g.n0 == 0 && g.div.pow2) {
+    // Empty seed graph, d = 2^l (every request of a typical serving mix): one shift each
+    // instead of two 64-bit multiply-highs.
+    const uint32_t l = g.div.l;
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x & 31; j < len; j += 32)
+      store_pair<Narrow>(out, out0 + j, (base + j) >> l, static_cast<uint64_t>(stage[j]) >> (l + 1));
   } else {
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
       const uint64_t i = base + j;
