@@ -96,6 +96,15 @@ def test_64_bit_positions_far_into_a_large_graph(ba):
                                       opar.edges_range(77, n, d, 0, a, b))
 
 
+@pytest.mark.parametrize("seed,n,d,n0", [(81, 2**29, 13, 0), (83, 2**28, 24, 25), (85, 2**29, 8, 9)])
+def test_64_bit_positions_other_d_and_seed_cliques(ba, seed, n, d, n0):
+    # the 64-bit flush's general path (d not a power of two, or a seed clique)
+    m = ba.ba_num_edges(n, d, n0)
+    for a, b in [(m - 200_000, m), (2**31 - 500, 2**31 + 60_000)]:
+        np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
+                                      opar.edges_range(seed, n, d, n0, a, b))
+
+
 def test_host_output_matches_device_output(ba):
     g = W.PLAIN_SMALL
     host = torch.empty((g.m, 2), dtype=torch.int64).pin_memory()

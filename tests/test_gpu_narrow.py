@@ -22,7 +22,9 @@ def _gpu32(ba, seed, n, d, n0, a, b):
 CASES = [(1, 10**6, 4, 0, 0, 4 * 10**6), (3, 5000, 3, 0, 17, 14_983), (13, 1000, 4, 5, 0, 3990),
          (17, 500, 32, 33, 0, 528 + 467 * 32), (19, 200, 5, 1, 0, 995),
          (77, 2**29, 16, 0, 2**33 - 300_000, 2**33),            # 64-bit positions
-         (79, 2**31, 2, 0, 2**32 - 5000, 2**32)]                # node IDs up to 2^31 - 1
+         (79, 2**31, 2, 0, 2**32 - 5000, 2**32),                # node IDs up to 2^31 - 1
+         (81, 2**29, 13, 0, 13 * 2**29 - 100_000, 13 * 2**29),  # 64-bit, d not a power of 2
+         (83, 2**28, 24, 25, 300 + (2**28 - 25) * 24 - 100_000, 300 + (2**28 - 25) * 24)]
 
 
 @pytest.mark.parametrize("seed,n,d,n0,a,b", CASES)
