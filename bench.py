@@ -282,15 +282,17 @@ def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
 
 # ---------------------------------------------------------------------- GPU arm --
 
+KERNEL_SOURCES = ("ba_device.cuh", "ba_draw.cuh", "ba_kernels.cu")
+
+
 def source_digest() -> str:
-    """Hash of the CUDA sources with comments and blank lines removed, so that recorded
-    ncu figures stay attached to the code they measured across comment-only edits."""
+    """Hash of the kernels' sources (device code and launchers) with comments and blank
+    lines removed, so that recorded ncu figures stay attached to the code they measured
+    across comment-only edits and host-side changes elsewhere."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1602_07106_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if not name.endswith((".cu", ".cuh", ".h")):
-            continue
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), encoding="utf-8") as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)

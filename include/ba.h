@@ -34,6 +34,10 @@
  *    BA_ERR_CUDA; ba_last_error_message() then gives its text (per thread).
  *  - Calls that take the same output pointer on different streams race; calls on
  *    different streams with different outputs may overlap freely.
+ *  - Per-call scratch (a tile counter; staging buffers of ba_generate_edges_host) comes
+ *    from a stream-ordered memory pool that libba creates per device on first use and
+ *    keeps for the life of the process; it holds on to at most 64 MB between calls, so
+ *    repeated small calls do not map device memory each time.
  */
 #ifndef BA_H
 #define BA_H

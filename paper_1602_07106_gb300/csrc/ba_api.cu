@@ -17,16 +17,51 @@ thread_local std::string g_last_error;
 
 // Per-call scratch from the stream-ordered allocator: freed on the same stream once the
 // work enqueued before the free has run, so concurrent calls never share it.
+// libba's own stream-ordered pool, one per device, created on first use and kept: it holds
+// on to up to 64 MB between calls (the default pool returns everything at each
+// synchronisation, and mapping it again costs more than a small call's kernel).
+std::mutex g_pool_mutex;
+std::vector<cudaMemPool_t> g_pools;
+
+cudaError_t library_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (g_pools.size() <= static_cast<size_t>(dev)) g_pools.resize(dev + 1, nullptr);
+  if (g_pools[dev] == nullptr) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = 64ull << 20;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
 struct StreamScratch {
   void *ptr = nullptr;
   cudaStream_t stream = nullptr;
   ba_status alloc(size_t bytes, cudaStream_t s) {
     stream = s;
-    cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+    e = cudaMallocFromPoolAsync(&ptr, bytes, pool, s);
     if (e != cudaSuccess) {
       ptr = nullptr;
-      return e == cudaErrorMemoryAllocation ? (set_error("cudaMallocAsync: out of memory"), BA_ERR_NOMEM)
-                                            : cuda_fail(e, "cudaMallocAsync");
+      return e == cudaErrorMemoryAllocation ? (set_error("cudaMallocFromPoolAsync: out of memory"), BA_ERR_NOMEM)
+                                            : cuda_fail(e, "cudaMallocFromPoolAsync");
     }
     return BA_OK;
   }
@@ -42,6 +77,14 @@ std::vector<int> g_sm_counts;
 }  // namespace
 
 void set_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+int adapt_tile(uint64_t total_edges, const Shape &s) {
+  const uint64_t warps = static_cast<uint64_t>(sm_count()) * std::max(s.ctas_per_sm, 1) *
+                         std::max(s.block / 32, 1);
+  int t = s.tile;
+  while (t > 256 && total_edges / static_cast<uint64_t>(t) < 4 * warps) t >>= 1;
+  return t;
+}
 
 ba_status cuda_fail(cudaError_t e, const char *where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);

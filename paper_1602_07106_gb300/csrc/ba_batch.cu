@@ -35,9 +35,10 @@ struct ba_batch_plan {
 
 namespace {
 
-// Fills graphs/offsets/prefix of a plan from host descriptors.
+// Fills graphs/offsets/prefix of a plan from host descriptors; shape.tile is adapted to
+// the total work first (adapt_tile), and the launch must use the adapted shape.
 ba_status build_tables(const ba_graph_desc *descs, int32_t G, const int64_t *out_offsets,
-                       const Shape &shape, ba_batch_plan *p) {
+                       Shape &shape, ba_batch_plan *p) {
   if (G < 0 || (G > 0 && descs == nullptr)) {
     set_error("batch needs G >= 0 descriptors");
     return BA_ERR_INVALID_ARG;
@@ -48,6 +49,10 @@ ba_status build_tables(const ba_graph_desc *descs, int32_t G, const int64_t *out
   p->prefix.assign(G + 1, 0);
   p->r32 = true;
   p->has_seed = false;
+  uint64_t total = 0;  // valid ranges only; the loop below rejects the rest
+  for (int32_t g = 0; g < G; ++g)
+    if (descs[g].edge_end > descs[g].edge_begin) total += descs[g].edge_end - descs[g].edge_begin;
+  shape.tile = adapt_tile(total, shape);
   const uint64_t T = static_cast<uint64_t>(shape.tile);
   for (int32_t g = 0; g < G; ++g) {
     const ba_graph_desc &d = descs[g];

@@ -44,6 +44,10 @@ GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint
                         uint64_t end);
 ba_status validate_graph(uint64_t n, uint32_t d, uint64_t n0, uint64_t *m_out);
 int sm_count();
+// Tile size for a batched launch of `total_edges` edges with shape s: the shape's tile,
+// halved (down to 256) until every warp of a full grid has about four tiles, as plain
+// calls do, so that small batches and light serving ticks still spread over the GPU.
+int adapt_tile(uint64_t total_edges, const Shape &s);
 
 // ---- tuner cache (ba_tune.cu)
 Shape shape_for(int kind, bool r32);

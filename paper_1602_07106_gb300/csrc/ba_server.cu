@@ -174,6 +174,17 @@ void prepare_tick(ba_server *s, TickSlot &slot, TickPlan &plan) {
   pre[0][0] = pre[1][0] = 0;
   plan.shape[0] = shape_for(BA_KIND_BATCH, true);
   plan.shape[1] = shape_for(BA_KIND_BATCH, false);
+  // This tick's work per position path, then tiles sized to it (a light tick still spreads
+  // over the GPU; see adapt_tile).
+  uint64_t work[2] = {0, 0};
+  for (uint64_t ticket : s->running) {
+    const Request &r = s->reqs[ticket];
+    const uint64_t a = r.desc.edge_begin + r.cursor;
+    const uint64_t b = std::min(r.desc.edge_begin + r.len, a + s->cfg.chunk_edges);
+    work[b <= (1ull << 31) ? 0 : 1] += b - a;
+  }
+  plan.shape[0].tile = adapt_tile(work[0], plan.shape[0]);
+  plan.shape[1].tile = adapt_tile(work[1], plan.shape[1]);
   const uint64_t tiles[2] = {static_cast<uint64_t>(plan.shape[0].tile),
                              static_cast<uint64_t>(plan.shape[1].tile)};
   std::vector<uint64_t> still;
