@@ -91,3 +91,24 @@ def test_uniform_over_positions():
     i = np.arange(1, 200_001, dtype=np.int64)
     frac = np.array([oracle.h(3, 2 * int(k) + 1) / (2 * int(k) + 1) for k in i])
     assert stats.kstest(frac, "uniform").pvalue > 1e-6
+
+
+def test_hash_equals_a_big_integer_statement():
+    # a third statement of h in Python integers (the C oracle and the CUDA library are the
+    # other two): SplitMix64 finaliser of seed ^ (r*G mod 2^64), then floor(z*r / 2^64)
+    M = (1 << 64) - 1
+
+    def h_big(seed, r):
+        z = seed ^ ((r * G) & M)
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        return (z * r) >> 64
+
+    rng = np.random.default_rng(11)
+    pairs = [(int(s), int(r)) for s, r in zip(rng.integers(0, 2**63, 10_000, dtype=np.int64),
+                                               rng.integers(1, 2**63, 10_000, dtype=np.int64))]
+    pairs += [(s, r) for s in (0, 1, 2**64 - 1) for r in (1, 2**32 - 1, 2**32 + 1, 2**41 + 1,
+                                                         2**63 - 1)]
+    for s, r in pairs:
+        assert oracle.h(s, r) == h_big(s, r), (s, r)
