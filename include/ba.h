@@ -72,7 +72,8 @@ const char *ba_last_error_message(void);
 int ba_version(void);
 
 /* m = n0(n0-1)/2 + (n-n0) d (section 4), or 0 when (n, d, n0) breaks the argument rules
- * or m > 2^62. */
+ * or m > 2^62.  A valid graph can have m = 0 too (n = n0 = 1); a call with an empty range,
+ * e.g. ba_generate_edges(..., 0, 0, NULL, ...), tells the two apart by its status. */
 uint64_t ba_num_edges(uint64_t n, uint32_t d, uint64_t n0);
 
 /*
@@ -298,10 +299,10 @@ typedef struct ba_server ba_server;
 typedef struct ba_server_config {
     uint64_t memory_budget_bytes;  /* device bytes for output buffers (0 = 50% of free) */
     uint64_t chunk_edges;          /* edges per request per tick (0 = 1<<24) */
-    int32_t max_active;            /* requests on the device at once (0 = 256) */
-    int32_t max_inflight_ticks;    /* ticks enqueued ahead of the GPU (0 = 2) */
+    int32_t max_active;            /* requests on the device at once (0 = 256; <= 65536) */
+    int32_t max_inflight_ticks;    /* ticks enqueued ahead of the GPU (0 = 2; <= 64) */
     int32_t device;                /* CUDA device ordinal (-1 = current) */
-    int32_t reserved;
+    int32_t max_queued;            /* requests waiting for admission (0 = no limit) */
 } ba_server_config;
 
 typedef struct ba_server_stats {
@@ -317,20 +318,22 @@ enum { BA_REQ_QUEUED = 0, BA_REQ_RUNNING = 1, BA_REQ_DONE = 2, BA_REQ_FAILED = 3
  * memory budget and max_active allow, and on every tick packs the next chunk of every
  * running request into one batched launch (ba_batch plan machinery), so that requests
  * arriving while others run join the next tick.  Output buffers live on the device until
- * ba_server_release.
+ * ba_server_release.  A config field outside its limits gives BA_ERR_INVALID_ARG.
  */
 ba_status ba_server_create(const ba_server_config *cfg, ba_server **server);
 
 /* Queues a request (n0 must be 0 or a clique seed graph like every other call); returns
- * its ticket.  BA_ERR_NOMEM if the request alone exceeds the budget. */
+ * its ticket.  BA_ERR_NOMEM if the request alone exceeds the budget; BA_ERR_BUSY (counted
+ * in rejected_busy) if max_queued requests already wait for admission -- retry later. */
 ba_status ba_server_submit(ba_server *server, const ba_graph_desc *req, uint64_t *ticket);
 
-/* State (BA_REQ_*) of a ticket; for DONE/FAILED also the submit-to-completion latency in
- * nanoseconds (latency_ns may be NULL). */
+/* State (BA_REQ_*) of a ticket and, for DONE, its submit-to-completion latency in
+ * nanoseconds (0 in the other states; latency_ns may be NULL). */
 ba_status ba_server_poll(ba_server *server, uint64_t ticket, int32_t *state,
                          uint64_t *latency_ns);
 
-/* Blocks until the ticket is DONE or FAILED or timeout_ms passes (BA_ERR_TIMEOUT). */
+/* Blocks until the ticket is DONE (BA_OK) or FAILED (BA_ERR_CUDA) or timeout_ms passes
+ * (BA_ERR_TIMEOUT); timeout_ms <= 0 only checks the state once. */
 ba_status ba_server_wait(ba_server *server, uint64_t ticket, int64_t timeout_ms);
 
 /* Device pointer and edge count of a DONE request (valid until ba_server_release). */
@@ -346,8 +349,9 @@ ba_status ba_server_release(ba_server *server, uint64_t ticket);
 
 ba_status ba_server_stats_get(ba_server *server, ba_server_stats *stats);
 
-/* Stops the scheduler (queued requests are dropped, running ones finish), frees all
- * buffers. */
+/* Stops the scheduler: the ticks already enqueued finish, no further chunk is issued,
+ * queued and unfinished requests are dropped; then frees every buffer, including the
+ * results not yet released. */
 ba_status ba_server_destroy(ba_server *server);
 
 #ifdef __cplusplus

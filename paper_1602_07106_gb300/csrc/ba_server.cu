@@ -290,6 +290,11 @@ ba_status ba_server_create(const ba_server_config *cfg, ba_server **server) {
   ba_server *s = new (std::nothrow) ba_server();
   if (!s) return BA_ERR_NOMEM;
   if (cfg) s->cfg = *cfg;
+  if (s->cfg.max_active > 65536 || s->cfg.max_inflight_ticks > 64 || s->cfg.max_queued < 0) {
+    delete s;
+    set_error("server config: max_active <= 65536, max_inflight_ticks <= 64, max_queued >= 0");
+    return BA_ERR_INVALID_ARG;
+  }
   if (s->cfg.device < 0) cudaGetDevice(&s->device); else s->device = s->cfg.device;
   if (s->cfg.chunk_edges == 0) s->cfg.chunk_edges = 1ull << 24;
   if (s->cfg.max_active <= 0) s->cfg.max_active = 256;
@@ -357,6 +362,11 @@ ba_status ba_server_submit(ba_server *s, const ba_graph_desc *req, uint64_t *tic
       set_error("server stopped after a CUDA error");
       return BA_ERR_CUDA;
     }
+    if (len > 0 && s->cfg.max_queued > 0 && s->queue.size() >= static_cast<size_t>(s->cfg.max_queued)) {
+      s->stats.rejected_busy++;
+      set_error("admission queue full (max_queued)");
+      return BA_ERR_BUSY;
+    }
     const uint64_t t = s->next_ticket++;
     Request r;
     r.desc = *req;
@@ -399,7 +409,9 @@ ba_status ba_server_wait(ba_server *s, uint64_t ticket, int64_t timeout_ms) {
     return BA_ERR_INVALID_ARG;
   }
   std::unique_lock<std::mutex> lk(s->mu);
-  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  // clamped so that the deadline cannot overflow the clock (2^40 ms is 35 years)
+  const int64_t ms = std::min<int64_t>(std::max<int64_t>(timeout_ms, 0), int64_t{1} << 40);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(ms);
   for (;;) {
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) {

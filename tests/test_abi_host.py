@@ -137,3 +137,7 @@ def test_batch_and_server_argument_rules():
                              offsets=[0, 4, 9], stream=0)               # graph 0 does not fit
     assert e.value.status == ba.BA_ERR_INVALID_ARG
     ba.ba_generate_batch([], out=None, stream=0)                         # nothing to do
+    for bad in ({"max_active": 65537}, {"max_inflight_ticks": 65}, {"max_queued": -1}):
+        with pytest.raises(ba.BAError) as e:                             # before any CUDA call
+            ba.ba_server_create(**bad)
+        assert e.value.status == ba.BA_ERR_INVALID_ARG, bad

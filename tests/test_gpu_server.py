@@ -88,6 +88,32 @@ def test_admission_waits_for_memory_and_never_hangs(ba):
         ba.ba_server_destroy(srv)
 
 
+def test_full_admission_queue_answers_busy(ba):
+    # budget for one 1M-edge request and room for one waiting request: A runs (and holds the
+    # budget until released), B waits, C is turned away until the queue has room again
+    srv = ba.ba_server_create(memory_budget_bytes=16 * 2**20, chunk_edges=1 << 18, max_active=4,
+                              max_queued=1)
+    try:
+        a = ba.ba_server_submit(srv, 200, 2**22, 4, 0, 0, 2**20)
+        ba.ba_server_wait(srv, a, 60_000)
+        b = ba.ba_server_submit(srv, 201, 2**22, 4, 0, 2**20, 2**21)
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_submit(srv, 202, 2**22, 4, 0, 0, 2**20)
+        assert e.value.status == ba.BA_ERR_BUSY
+        empty = ba.ba_server_submit(srv, 203, 2**22, 4, 0, 5, 5)   # nothing to queue: done at once
+        assert ba.ba_server_poll(srv, empty)[0] == ba.BA_REQ_DONE
+        assert ba.ba_server_stats_get(srv)["rejected_busy"] == 1
+        ba.ba_server_release(srv, a)
+        ba.ba_server_wait(srv, b, 60_000)
+        assert torch.equal(ba.server_result_tensor(srv, b), _plain(ba, 201, 2**22, 4, 0, 2**20, 2**21))
+        ba.ba_server_release(srv, b)
+        c = ba.ba_server_submit(srv, 202, 2**22, 4, 0, 0, 2**20)
+        ba.ba_server_wait(srv, c, 60_000)
+        assert torch.equal(ba.server_result_tensor(srv, c), _plain(ba, 202, 2**22, 4, 0, 0, 2**20))
+    finally:
+        ba.ba_server_destroy(srv)
+
+
 def test_autotuner_picks_a_valid_shape_and_output_is_unchanged(ba):
     n, d = 2**20, 8
     m = n * d
