@@ -252,15 +252,17 @@ uint64_t ba_batch_plan_total_edges(const ba_batch_plan *plan);
 ba_status ba_batch_plan_offsets(const ba_batch_plan *plan, int64_t *host_offsets);
 
 /* Replays the plan's CUDA graph on `stream`, writing into out_dev (16-byte aligned,
- * 2*total_edges int64).  The first call (and any call with another stream or out_dev)
- * captures or updates the graph. */
+ * 2*total_edges int64).  The first call, and any call with another out_dev, captures the
+ * graph again.  Launches of one plan share its tile counter: let one finish before the
+ * next starts (same stream, or an event between them). */
 ba_status ba_batch_plan_launch(ba_batch_plan *plan, int64_t *out_dev, void *stream);
 
-/* Waits for nothing; frees the plan's device tables and graph after the device work
- * already enqueued with it. */
+/* Frees the plan's device tables and graph; cudaFree waits for the device work already
+ * enqueued, so a plan may be destroyed right after its last launch. */
 ba_status ba_batch_plan_destroy(ba_batch_plan *plan);
 
-/* One-shot form: plan, launch once, destroy.  offsets_host as in ba_batch_plan_create. */
+/* One-shot form: plan, launch once, destroy.  offsets_host as in ba_batch_plan_create.
+ * Its tables come from libba's pool; synchronises `stream` before returning. */
 ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
                             const int64_t *offsets_host, int64_t *out_dev,
                             const ba_tuning *tune, void *stream);

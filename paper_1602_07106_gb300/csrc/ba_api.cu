@@ -54,16 +54,7 @@ struct StreamScratch {
   cudaStream_t stream = nullptr;
   ba_status alloc(size_t bytes, cudaStream_t s) {
     stream = s;
-    cudaMemPool_t pool = nullptr;
-    cudaError_t e = library_pool(&pool);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
-    e = cudaMallocFromPoolAsync(&ptr, bytes, pool, s);
-    if (e != cudaSuccess) {
-      ptr = nullptr;
-      return e == cudaErrorMemoryAllocation ? (set_error("cudaMallocFromPoolAsync: out of memory"), BA_ERR_NOMEM)
-                                            : cuda_fail(e, "cudaMallocFromPoolAsync");
-    }
-    return BA_OK;
+    return pool_alloc(&ptr, bytes, s);
   }
   void release() {
     if (ptr) cudaFreeAsync(ptr, stream);
@@ -77,6 +68,21 @@ std::vector<int> g_sm_counts;
 }  // namespace
 
 void set_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+ba_status pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+  *ptr = nullptr;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = library_pool(&pool);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+  e = cudaMallocFromPoolAsync(ptr, bytes, pool, s);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    if (e != cudaErrorMemoryAllocation) return cuda_fail(e, "cudaMallocFromPoolAsync");
+    set_error("cudaMallocFromPoolAsync: out of memory");
+    return BA_ERR_NOMEM;
+  }
+  return BA_OK;
+}
 
 int adapt_tile(uint64_t total_edges, const Shape &s) {
   const uint64_t warps = static_cast<uint64_t>(sm_count()) * std::max(s.ctas_per_sm, 1) *

@@ -221,8 +221,9 @@ ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G, const int64_t
   const size_t gbytes = p.graphs.size() * sizeof(GraphDev);
   const size_t bytes = gbytes + p.prefix.size() * sizeof(uint64_t) + 256;
   void *mem = nullptr;
-  cudaError_t e = cudaMallocAsync(&mem, bytes, s);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? BA_ERR_NOMEM : cuda_fail(e, "cudaMallocAsync");
+  st = pool_alloc(&mem, bytes, s);
+  if (st != BA_OK) return st;
+  cudaError_t e;
   char *base = static_cast<char *>(mem);
   GraphDev *dg = reinterpret_cast<GraphDev *>(base);
   uint64_t *dp = reinterpret_cast<uint64_t *>(base + gbytes);

@@ -44,6 +44,9 @@ GraphDev make_graph_dev(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint
                         uint64_t end);
 ba_status validate_graph(uint64_t n, uint32_t d, uint64_t n0, uint64_t *m_out);
 int sm_count();
+// Stream-ordered scratch from libba's own pool on the current device (kept mapped up to
+// 64 MB between calls); release with cudaFreeAsync on the same stream.
+ba_status pool_alloc(void **ptr, size_t bytes, cudaStream_t s);
 // Tile size for a batched launch of `total_edges` edges with shape s: the shape's tile,
 // halved (down to 256) until every warp of a full grid has about four tiles, as plain
 // calls do, so that small batches and light serving ticks still spread over the GPU.

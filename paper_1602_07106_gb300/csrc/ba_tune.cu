@@ -297,13 +297,13 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
   const bool r32 = edge_end <= (1ull << 31);
   const uint64_t node_limit = std::min<uint64_t>(n, 100000);
   void *counter = nullptr, *counts = nullptr, *tab_mem = nullptr;
-  cudaError_t e = cudaMallocAsync(&counter, 256, s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  ba_status ast = pool_alloc(&counter, 256, s);
+  if (ast != BA_OK) return ast;
   if (kind == BA_KIND_DEGREE) {
-    e = cudaMallocAsync(&counts, node_limit * sizeof(uint64_t), s);
-    if (e != cudaSuccess) {
+    ast = pool_alloc(&counts, node_limit * sizeof(uint64_t), s);
+    if (ast != BA_OK) {
       cudaFreeAsync(counter, s);
-      return cuda_fail(e, "cudaMallocAsync");
+      return ast;
     }
   }
   // A batch of 64 slices of the sample range exercises the batched kernel.
@@ -316,10 +316,10 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
       g.out_edge = a - edge_begin;
       graphs.push_back(g);
     }
-    e = cudaMallocAsync(&tab_mem, graphs.size() * sizeof(GraphDev) + (graphs.size() + 1) * 8, s);
-    if (e != cudaSuccess) {
+    ast = pool_alloc(&tab_mem, graphs.size() * sizeof(GraphDev) + (graphs.size() + 1) * 8, s);
+    if (ast != BA_OK) {
       cudaFreeAsync(counter, s);
-      return cuda_fail(e, "cudaMallocAsync");
+      return ast;
     }
   }
   const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
