@@ -83,6 +83,14 @@ def _load():
         lib.ora_degree_count_range_variant.argtypes = [_u64, _u64, _u32, _u64,
                                                        ctypes.c_int, ctypes.c_int, _u64,
                                                        _u64, _u64, _ptr]
+        lib.ora_edges_simple.restype = ctypes.c_int
+        lib.ora_edges_simple.argtypes = [_u64, _u64, _u32, _u64, ctypes.c_int, _ptr, _ptr]
+        lib.ora_edges_range_simple.restype = ctypes.c_int
+        lib.ora_edges_range_simple.argtypes = [_u64, _u64, _u32, _u64, ctypes.c_int, _u64,
+                                               _u64, _ptr]
+        lib.ora_degree_count_range_simple.restype = ctypes.c_int
+        lib.ora_degree_count_range_simple.argtypes = [_u64, _u64, _u32, _u64, ctypes.c_int,
+                                                      _u64, _u64, _u64, _ptr]
         _lib = lib
         return lib
 
@@ -217,4 +225,44 @@ def degree_count_range_variant(seed: int, n: int, d: int, n0: int, family: int,
     _check(_load().ora_degree_count_range_variant(seed, n, d, n0, family,
                                                   int(no_self_loops), a, b, node_limit,
                                                   _p(counts)), "degree_count_range_variant")
+    return counts
+
+
+# Graphs without parallel edges (section 4: a node's duplicate targets are rejected).
+REDRAW_SALT = 0xD6E8FEB86659FD93
+REDRAW_CAP = 65536
+
+
+def edges_simple(seed: int, n: int, d: int, n0: int, no_self_loops: bool) -> np.ndarray:
+    """All m edges, shape (m, 2), of the graph whose nodes reject duplicate targets, built
+    on the stored array without rejection that the chains follow."""
+    m = num_edges(n, d, n0)
+    if m == 0:
+        raise ValueError("oracle edges_simple: invalid graph parameters")
+    E = np.empty(2 * m, dtype=np.int64)
+    out = np.empty((m, 2), dtype=np.int64)
+    _check(_load().ora_edges_simple(seed, n, d, n0, int(no_self_loops), _p(E), _p(out)),
+           "edges_simple")
+    return out
+
+
+def edges_range_simple(seed: int, n: int, d: int, n0: int, no_self_loops: bool, a: int,
+                       b: int) -> np.ndarray:
+    """Edges a..b-1 of that graph, shape (b-a, 2), recomputed without the array."""
+    out = np.empty((max(b - a, 0), 2), dtype=np.int64)
+    _check(_load().ora_edges_range_simple(seed, n, d, n0, int(no_self_loops), a, b, _p(out)),
+           "edges_range_simple")
+    return out
+
+
+def degree_count_range_simple(seed: int, n: int, d: int, n0: int, no_self_loops: bool, a: int,
+                              b: int, node_limit: int,
+                              counts: np.ndarray | None = None) -> np.ndarray:
+    """Degrees of nodes 0..node_limit-1 over edges a..b-1 of that graph."""
+    if counts is None:
+        counts = np.zeros(node_limit, dtype=np.uint64)
+    assert counts.dtype == np.uint64 and counts.size == node_limit
+    _check(_load().ora_degree_count_range_simple(seed, n, d, n0, int(no_self_loops), a, b,
+                                                 node_limit, _p(counts)),
+           "degree_count_range_simple")
     return counts

@@ -22,14 +22,16 @@
  *   h = floor(z * r / 2^64)   (Lemire's multiply-shift reduction to 0..r-1).
  *
  * Variants (the second half of this file): hash_crc of Fig. 3 (CRC-32C of r twice, then
- * the remainder mod r) in place of h, and the self-loop-free graph of section 4, where
- * the draw for edge i ranges only over the positions of the edges of earlier nodes.
+ * the remainder mod r) in place of h, the self-loop-free graph of section 4, where the
+ * draw for edge i ranges only over the positions of the edges of earlier nodes, and the
+ * graph of section 4 whose nodes reject duplicate targets (no parallel edges).
  *
  * Errors: every entry point returns 0 on success and a negative value when the
  * parameters do not describe a graph (d = 0, n0 > n, n = 0, 2m + 1 >= 2^64, or an
  * edge range outside 0..m).  Buffers belong to the caller.
  */
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef unsigned __int128 u128;
@@ -371,6 +373,157 @@ int ora_degree_count_range_variant(uint64_t seed, uint64_t n, uint32_t d, uint64
                                                       no_self_loops, 2 * i + 1);
         if (u < node_limit) counts[u] += 1;
         if (v < node_limit) counts[v] += 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------ graphs without parallel edges -- */
+
+/*
+ * Section 4 avoids parallel edges by keeping the targets already generated for the
+ * current node in a table of at most d entries and rejecting a target that is already
+ * there.  The paper does not say how a rejected draw is replaced, nor what an odd
+ * position reached by a later chain means; the reading taken here:
+ *  - A chain resolves every position by the array without rejection (the plain or the
+ *    self-loop-free E above): generateEdge's recursion cannot see rejections made while
+ *    another node's edges were generated.  Only the output of a node changes.
+ *  - Node u >= n0 takes its edges in ID order j = 0..d-1 (edge i = first + j).  The
+ *    candidate is E[2i+1].  While it is already among the node's accepted targets, fewer
+ *    than REDRAW_CAP redraws were made, and j < reach(u), redraw k (k = 1, 2, ...) draws
+ *    x over the same range as the plain draw, keyed by 2i+1, with the SplitMix64 bits of
+ *    seed XOR k * REDRAW_SALT, and the candidate becomes E[x].  The candidate left at the
+ *    end is the edge's target.
+ *  - reach(u) is the number of distinct nodes the draw can reach: with self-loops all of
+ *    0..u except an isolated node 0 (n0 = 1), without self-loops the u nodes before u.
+ *    A node with d > reach(u) keeps the duplicates beyond its reach (nothing else exists).
+ */
+#define ORA_REDRAW_SALT 0xD6E8FEB86659FD93ULL
+#define ORA_REDRAW_CAP 65536u
+
+static uint64_t distinct_reach(uint64_t node, uint64_t n0, int no_self_loops)
+{
+    if (no_self_loops) return node;
+    return n0 == 1 ? node : node + 1;
+}
+
+/* E[p] of the array without rejection, from a stored array or by recomputation. */
+struct ora_positions {
+    const int64_t *E;  /* NULL: recompute */
+    uint64_t seed, n0, m0;
+    uint32_t d;
+    int no_self_loops;
+};
+
+static int64_t position_of(const struct ora_positions *P, uint64_t p)
+{
+    if (P->E) return P->E[p];
+    return variant_position_value(P->seed, P->d, P->n0, P->m0, ORA_HASH_SPLITMIX,
+                                  P->no_self_loops, p);
+}
+
+static int already_taken(const int64_t *t, uint64_t count, int64_t v)
+{
+    for (uint64_t l = 0; l < count; l++)
+        if (t[l] == v) return 1;
+    return 0;
+}
+
+/* Targets of the first `count` edges of node `node` (count <= d) under the rule above. */
+static void node_targets_simple(const struct ora_positions *P, uint64_t node, uint64_t count,
+                                int64_t *t)
+{
+    uint64_t first = P->m0 + (node - P->n0) * P->d;
+    uint64_t reach = distinct_reach(node, P->n0, P->no_self_loops);
+    for (uint64_t j = 0; j < count; j++) {
+        uint64_t q = 2 * (first + j) + 1;
+        int64_t v = position_of(P, q);
+        uint32_t k = 0;
+        while (j < reach && k < ORA_REDRAW_CAP && already_taken(t, j, v)) {
+            k++;
+            uint64_t range = draw_range(P->no_self_loops, P->d, P->n0, P->m0, q);
+            uint64_t x = ora_draw(ORA_HASH_SPLITMIX, P->seed ^ ((uint64_t)k * ORA_REDRAW_SALT),
+                                  q, range);
+            v = position_of(P, x);
+        }
+        t[j] = v;
+    }
+}
+
+/*
+ * The whole graph without parallel edges: out[2m] pairs (source, target).  E (2m int64,
+ * caller's workspace) receives the array without rejection that the chains follow.
+ */
+int ora_edges_simple(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, int no_self_loops,
+                     int64_t *E, int64_t *out)
+{
+    if (ora_bb_array_variant(seed, n, d, n0, ORA_HASH_SPLITMIX, no_self_loops, E) != 0)
+        return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    struct ora_positions P = {E, seed, n0, m0, d, no_self_loops};
+    int64_t *t = malloc((size_t)d * sizeof(int64_t));
+    if (t == NULL) return -1;
+    for (uint64_t i = 0; i < m0; i++) {
+        out[2 * i] = E[2 * i];
+        out[2 * i + 1] = E[2 * i + 1];
+    }
+    for (uint64_t node = n0; node < n; node++) {
+        uint64_t first = m0 + (node - n0) * d;
+        node_targets_simple(&P, node, d, t);
+        for (uint64_t j = 0; j < d; j++) {
+            out[2 * (first + j)] = (int64_t)node;
+            out[2 * (first + j) + 1] = t[j];
+        }
+    }
+    free(t);
+    return 0;
+}
+
+/* Edges a..b-1 of the graph without parallel edges, without the array: each node that
+ * owns an edge in range has its targets recomputed from its first edge on. */
+int ora_edges_range_simple(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                           int no_self_loops, uint64_t a, uint64_t b, int64_t *out)
+{
+    if (!variant_ok(n, d, n0, ORA_HASH_SPLITMIX, no_self_loops)) return -1;
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (a > b || b > m) return -1;
+    uint64_t m0 = (uint64_t)seed_edges(n0);
+    struct ora_positions P = {NULL, seed, n0, m0, d, no_self_loops};
+    int64_t *t = malloc((size_t)d * sizeof(int64_t));
+    if (t == NULL) return -1;
+    uint64_t i = a;
+    for (; i < b && i < m0; i++) {
+        out[2 * (i - a)] = seed_clique_position(2 * i);
+        out[2 * (i - a) + 1] = seed_clique_position(2 * i + 1);
+    }
+    while (i < b) {
+        uint64_t node = n0 + (i - m0) / d;
+        uint64_t first = m0 + (node - n0) * d;
+        uint64_t stop = first + d < b ? first + d : b;
+        node_targets_simple(&P, node, stop - first, t);
+        for (; i < stop; i++) {
+            out[2 * (i - a)] = (int64_t)node;
+            out[2 * (i - a) + 1] = t[i - first];
+        }
+    }
+    free(t);
+    return 0;
+}
+
+/* counts[j] += end points equal to j among edges a..b-1 of the graph without parallel
+ * edges (a self-loop counts twice), for j < node_limit. */
+int ora_degree_count_range_simple(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                  int no_self_loops, uint64_t a, uint64_t b,
+                                  uint64_t node_limit, uint64_t *counts)
+{
+    if (!variant_ok(n, d, n0, ORA_HASH_SPLITMIX, no_self_loops)) return -1;
+    uint64_t m = ora_num_edges(n, d, n0);
+    if (a > b || b > m) return -1;
+    int64_t pair[2 * 4096];
+    for (uint64_t lo = a; lo < b; lo += 4096) {
+        uint64_t hi = b - lo < 4096 ? b : lo + 4096;
+        if (ora_edges_range_simple(seed, n, d, n0, no_self_loops, lo, hi, pair) != 0) return -1;
+        for (uint64_t k = 0; k < 2 * (hi - lo); k++)
+            if ((uint64_t)pair[k] < node_limit) counts[pair[k]] += 1;
     }
     return 0;
 }
