@@ -144,10 +144,23 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
  *                            the edges before the first edge of edge i's node, so every
  *                            target is an earlier node.  Needs n0 >= 2 (the first new
  *                            node must have a seed edge to attach to).
- * The flags combine.  Unknown flags, or NO_SELF_LOOPS with n0 < 2, give
- * BA_ERR_INVALID_ARG. */
+ *  BA_VARIANT_NO_PARALLEL_EDGES  section 4's rejection of duplicate targets: node u takes
+ *                            its d edges in order and an edge whose target one of its
+ *                            earlier edges already has draws again -- redraw k over the
+ *                            same range, keyed by 2i+1, with the SplitMix64 bits of
+ *                            seed XOR k * 0xD6E8FEB86659FD93, then the chain of Fig. 1
+ *                            from the drawn position -- until the target is new, as long
+ *                            as a new one exists (edge j < reach(u): u+1 nodes, u with
+ *                            n0 = 1 or NO_SELF_LOOPS) and for at most 65536 redraws.
+ *                            Chains follow the array without rejection, so only the
+ *                            node's own output changes.  Needs d <= 32; combines with
+ *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH;
+ *                            generation only (ba_degree_count_variant rejects it).
+ * The flags combine as stated.  Unknown flags, NO_SELF_LOOPS with n0 < 2, or
+ * NO_PARALLEL_EDGES outside its limits give BA_ERR_INVALID_ARG. */
 #define BA_VARIANT_CRC_HASH 1u
 #define BA_VARIANT_NO_SELF_LOOPS 2u
+#define BA_VARIANT_NO_PARALLEL_EDGES 4u
 
 /* ba_generate_edges for a variant graph (same arguments, layout and errors, plus the
  * flags).  variant = 0 is ba_generate_edges itself. */

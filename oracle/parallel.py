@@ -94,3 +94,21 @@ def degree_count_range_variant(seed, n, d, n0, family, no_loops, a, b, limit,
     with mp.get_context("spawn").Pool(workers) as pool:
         parts = pool.map(_variant_degrees_piece, jobs)
     return np.sum(parts, axis=0, dtype=np.uint64)
+
+
+def _simple_edges_piece(args):
+    seed, n, d, n0, no_loops, a, b = args
+    return oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b)
+
+
+def edges_range_simple(seed, n, d, n0, no_loops, a, b, workers: int | None = None) -> np.ndarray:
+    """oracle.edges_range_simple (no parallel edges) over [a, b), split across processes;
+    each piece recomputes the node it starts inside, so any cut gives the same edges."""
+    workers = workers or default_workers()
+    if workers == 1 or b - a < 4_000_000:
+        return oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b)
+    oracle.build()
+    jobs = [(seed, n, d, n0, no_loops, x, y) for x, y in _cuts(a, b, 4 * workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_simple_edges_piece, jobs)
+    return np.concatenate(parts, axis=0)

@@ -27,7 +27,7 @@ BA_OK, BA_ERR_INVALID_ARG, BA_ERR_RANGE, BA_ERR_OVERFLOW = 0, 1, 2, 3
 BA_ERR_CUDA, BA_ERR_NOMEM, BA_ERR_TIMEOUT, BA_ERR_BUSY, BA_ERR_NOT_FOUND = 4, 5, 6, 7, 8
 BA_KIND_GENERATE, BA_KIND_DEGREE, BA_KIND_BATCH = 0, 1, 2
 BA_REQ_QUEUED, BA_REQ_RUNNING, BA_REQ_DONE, BA_REQ_FAILED = 0, 1, 2, 3
-BA_VARIANT_CRC_HASH, BA_VARIANT_NO_SELF_LOOPS = 1, 2
+BA_VARIANT_CRC_HASH, BA_VARIANT_NO_SELF_LOOPS, BA_VARIANT_NO_PARALLEL_EDGES = 1, 2, 4
 
 _u64, _u32, _i32, _i64 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64
 _vp = ctypes.c_void_p

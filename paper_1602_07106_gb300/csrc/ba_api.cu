@@ -281,15 +281,20 @@ ba_status ba_degree_count(uint64_t seed, uint64_t n, uint32_t d, uint64_t node_l
   return ba_degree_count_range(seed, n, d, 0, 0, m, node_limit, counts_dev, 0, stream);
 }
 
-// Checks the variant flags against the graph: known bits only, and a seed edge for the
-// self-loop-free rule.
-static ba_status check_variant(uint32_t variant, uint64_t n0) {
-  if ((variant & ~static_cast<uint32_t>(BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS)) != 0) {
+// Checks the variant flags against the graph: known bits only, a seed edge for the
+// self-loop-free rule, and the limits of the rejection of parallel edges.
+static ba_status check_variant(uint32_t variant, uint32_t d, uint64_t n0) {
+  if ((variant & ~static_cast<uint32_t>(BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS |
+                                        BA_VARIANT_NO_PARALLEL_EDGES)) != 0) {
     set_error("unknown variant flag");
     return BA_ERR_INVALID_ARG;
   }
   if ((variant & BA_VARIANT_NO_SELF_LOOPS) && n0 < 2) {
     set_error("the self-loop-free graph needs a seed graph with an edge (n0 >= 2)");
+    return BA_ERR_INVALID_ARG;
+  }
+  if ((variant & BA_VARIANT_NO_PARALLEL_EDGES) && ((variant & BA_VARIANT_CRC_HASH) || d > 32)) {
+    set_error("rejecting parallel edges needs d <= 32 and the SplitMix64 hash");
     return BA_ERR_INVALID_ARG;
   }
   return BA_OK;
@@ -305,7 +310,7 @@ ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint6
   uint64_t m = 0;
   ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
   if (st != BA_OK) return st;
-  st = check_variant(variant, n0);
+  st = check_variant(variant, d, n0);
   if (st != BA_OK) return st;
   if (edge_begin == edge_end) return BA_OK;
   if (out_dev == nullptr || (reinterpret_cast<uintptr_t>(out_dev) & 15) != 0) {
@@ -319,8 +324,11 @@ ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint6
   StreamScratch scratch;
   st = scratch.alloc(sizeof(unsigned long long), s);
   if (st != BA_OK) return st;
-  return launch_generate_variant(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr),
-                                 s, variant);
+  const uint32_t draw_flags = variant & (BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS);
+  st = launch_generate_variant(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr), s,
+                               draw_flags);
+  if (st != BA_OK || !(variant & BA_VARIANT_NO_PARALLEL_EDGES)) return st;
+  return launch_reject_duplicates(g, out_dev, s, (variant & BA_VARIANT_NO_SELF_LOOPS) != 0);
 }
 
 ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
@@ -331,8 +339,12 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
   uint64_t m = 0;
   ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
   if (st != BA_OK) return st;
-  st = check_variant(variant, n0);
+  st = check_variant(variant, d, n0);
   if (st != BA_OK) return st;
+  if (variant & BA_VARIANT_NO_PARALLEL_EDGES) {
+    set_error("degree counts of the graph without parallel edges are not supported");
+    return BA_ERR_INVALID_ARG;
+  }
   if (node_limit == 0) return BA_OK;
   if (counts_dev == nullptr || (reinterpret_cast<uintptr_t>(counts_dev) & 7) != 0) {
     set_error("counts must be a non-NULL, 8-byte aligned device pointer");

@@ -73,6 +73,10 @@ ba_status launch_generate_variant(const GraphDev &g, int64_t *out, const Shape &
 ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                                 int accumulate, const Shape &s, unsigned long long *counter,
                                 cudaStream_t stream, uint32_t variant);
+// Section 4's rejection of a node's duplicate targets over an output that the generate
+// kernel (plain, or self-loop-free with no_loops) has already written; d <= 32.
+ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
+                                   bool no_loops);
 ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,
                        int64_t *out, const Shape &s, unsigned long long *counter,
                        cudaStream_t stream);
