@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-sample-edges", type=int, default=2**28)
-    ap.add_argument("--profile", choices=["generate", "degree", "batch", "degree64", "crc"],
+    ap.add_argument("--profile", choices=["generate", "degree", "batch", "degree64", "crc",
+                                          "simple"],
                     default=None,
                     help="run a small case of one kernel (for ncu captures) and exit")
     ap.add_argument("--profile-edges", type=int, default=2**26)
@@ -90,6 +91,12 @@ def profile_case(args):
         for _ in range(args.profile_reps):
             ba.ba_generate_edges_variant(g.seed, g.n, g.d, 0, 0, e, ba.BA_VARIANT_CRC_HASH, out,
                                          stream)
+    elif args.profile == "simple":
+        # generate + section 4's rejection of duplicate targets (k_reject_duplicates)
+        out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
+        for _ in range(args.profile_reps):
+            ba.ba_generate_edges_variant(g.seed, g.n, g.d, 0, 0, e,
+                                         ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
     elif args.profile == "degree":
         # a slice from the middle of the graph: its share of targets below 1e5 (~2%) is
         # that of the whole graph, unlike a prefix
@@ -592,15 +599,19 @@ def extras(args, ba, torch, stream, main):
 
 
 def variants(ba, torch, stream, main):
-    """The variant graphs (hash_crc of Fig. 3, section 4's self-loop-free rule) on the
-    large workload's shape, and the streaming degree count with Fig. 3's hash."""
+    """The variant graphs (hash_crc of Fig. 3, section 4's self-loop-free rule and its
+    rejection of parallel edges) on the large workload's shape, and the streaming degree
+    count with Fig. 3's hash."""
     res = {}
     gl = W.PLAIN_LARGE
     plain_ms = main["kernels_ms"]["generate"]
+    P = ba.BA_VARIANT_NO_PARALLEL_EDGES
     cases = [("crc_hash", ba.BA_VARIANT_CRC_HASH, 0),
              ("no_self_loops", ba.BA_VARIANT_NO_SELF_LOOPS, gl.d + 1),
              ("crc_hash_no_self_loops", ba.BA_VARIANT_CRC_HASH | ba.BA_VARIANT_NO_SELF_LOOPS,
-              gl.d + 1)]
+              gl.d + 1),
+             ("no_parallel_edges", P, 0),
+             ("simple_graph", P | ba.BA_VARIANT_NO_SELF_LOOPS, gl.d + 1)]
     m_max = max(ba.ba_num_edges(gl.n, gl.d, n0) for _, _, n0 in cases)
     out = torch.empty((m_max, 2), dtype=torch.int64, device="cuda")
     for name, v, n0 in cases:
@@ -611,6 +622,14 @@ def variants(ba, torch, stream, main):
         t = statistics.median(ts)
         res[name] = {"workload": f"n=2^27 d=16 n0={n0} seed=42, all {m} edges as int64 pairs",
                      "edges_per_s": m / t, "ms": 1e3 * t, "vs_plain_generate": plain_ms / (1e3 * t)}
+        base = {"no_parallel_edges": None, "simple_graph": "no_self_loops"}.get(name, 0)
+        if base != 0:
+            # the rejection pass alone: this call minus the same graph without the flag;
+            # it reads every 16-byte pair back (targets sit between the sources)
+            base_ms = plain_ms if base is None else res[base]["ms"]
+            pass_ms = 1e3 * t - base_ms
+            res[name]["reject_pass_ms"] = pass_ms
+            res[name]["reject_pass_read_gbs"] = 16 * m / (pass_ms * 1e6) if pass_ms > 0 else None
     del out
     torch.cuda.empty_cache()
     g = W.STREAM_HUGE

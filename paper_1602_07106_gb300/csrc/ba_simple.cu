@@ -8,9 +8,9 @@
 // node (d <= 32, so a warp holds 32/d whole nodes):
 //   1. each lane holds its edge's target (read back from the output, or recomputed for
 //      the edges of the first node that lie before the range);
-//   2. __match_any_sync on (target) and on (node) finds the lanes whose target an earlier
-//      edge of the same node already has; a warp without such a lane is done;
-//   3. otherwise the node's edges are taken in order from the first duplicate on: while an
+//   2. each lane compares its target (low 32 bits) with those of the next d/2 edges of its
+//      node, cyclically, through shared memory; a warp without a repeat is done;
+//   3. otherwise the flagged nodes' edges are taken in order: while an
 //      edge's candidate is one of the targets accepted before it (a ballot over the node's
 //      lanes), j < reach(u) and fewer than kRedrawCap redraws were made, its lane redraws:
 //      the plain draw's range and key 2i+1 with the SplitMix64 bits of
@@ -29,9 +29,10 @@ constexpr uint64_t kRedrawSalt = 0xD6E8FEB86659FD93ull;
 constexpr uint32_t kRedrawCap = 65536u;
 
 // E[x] of the array without rejection: the chain of Fig. 1 (and section 4's seed test)
-// from position x.
+// from position x.  Out of line, like redraw: both run for a few edges in 10^4 and would
+// otherwise hold registers in the common path.
 template <class RT, bool HasSeed, class Draw>
-__device__ uint64_t array_value(RT x, const GraphDev &g, const Draw &draw, RT l2m0) {
+__device__ __noinline__ uint64_t array_value(RT x, const GraphDev &g, const Draw &draw, RT l2m0) {
   while (!chain_stops<RT, HasSeed>(x, l2m0)) x = draw(x);
   return target_of<RT, HasSeed>(x, g);
 }
@@ -39,60 +40,92 @@ __device__ uint64_t array_value(RT x, const GraphDev &g, const Draw &draw, RT l2
 // Candidate k >= 1 for edge i: a draw over the plain draw's range keyed by 2i+1 with the
 // salted seed, resolved through the array.
 template <class RT, bool HasSeed, class Draw>
-__device__ uint64_t redraw(uint64_t i, uint32_t k, const GraphDev &g, const Draw &draw, RT l2m0) {
+__device__ __noinline__ uint64_t redraw(uint64_t i, uint32_t k, const GraphDev &g, const Draw &draw, RT l2m0) {
   Draw salted = draw;
   salted.spre = seed_premix(g.seed ^ (static_cast<uint64_t>(k) * kRedrawSalt));
   return array_value<RT, HasSeed>(salted(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
 }
 
-// Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]; lane = slot * d + j.
+constexpr int kThreads = 256;
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+// Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]: the W = npw * d edges
+// i0 + item * W + lane (lane < W), i0 = the first edge of node n0 + q_lo; lane = slot*d + j.
 template <class RT, bool HasSeed, class Draw, bool NoLoop>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kThreads)
 k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, uint64_t q_hi,
                     uint32_t npw) {
+  // per warp: the low 32 bits of each node's targets, written twice in a row (entries j
+  // and j + d) so that lane j reads entry j + o for every offset o without a wrap; node s's
+  // row starts at word s * (d + 64), so the lanes of one read hit distinct banks (d >= 2:
+  // at most 16 rows, the last ending below word 1024)
+  __shared__ uint32_t key_rows[kThreads / 32][1024];
   Draw draw;
   draw.setup(g, nullptr, sizeof(RT) == 4);
   draw.bind(g);
   const RT l2m0 = seed_limit<RT>(g.two_m0);
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t d = g.d;
-  const uint32_t slot = lane / d;
+  const uint32_t W = npw * d;
+  const uint32_t slot = lane / d;  // < 16 since d >= 2
   const uint32_t j = lane - slot * d;
-  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t *row = key_rows[threadIdx.x >> 5] + slot * (d + 64) + j;  // used by lanes < W
+  const uint32_t half = d / 2;
+  const uint64_t i0 = g.m0 + q_lo * d;
   const uint64_t items = (q_hi - q_lo) / npw + 1;
-  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (uint64_t item = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-       item < items; item += warps) {
-    const uint64_t q = q_lo + item * npw + slot;
-    const uint64_t i = g.m0 + q * d + j;
-    const bool part = slot < npw && q <= q_hi && i < g.end;  // the edge or an earlier sibling is in range
-    const bool in_out = part && i >= g.begin;
-    long long *dst = reinterpret_cast<long long *>(out) + 2 * (in_out ? g.out_edge + (i - g.begin) : 0) + 1;
-    uint64_t t = 0;
-    if (in_out) t = static_cast<uint64_t>(__ldcs(dst));
-    else if (part) t = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
-    // node IDs are below 2^62, so the idle lanes' keys match nothing real
-    const uint32_t same_t = __match_any_sync(kAll, part ? t : ~0ull - lane);
-    const uint32_t same_node = __match_any_sync(kAll, part ? slot : 32u + lane);
-    const uint64_t node = g.n0 + q;
-    const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
-    const bool dup = part && j < reach && (same_t & same_node & lt) != 0;
-    uint32_t dups = __ballot_sync(kAll, dup);
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kThreads / 32);
+  const uint64_t step = warps * W;  // edges between a warp's consecutive items
+  long long *const tgt = reinterpret_cast<long long *>(out) + 1;  // targets: stride 2
+  uint64_t item = static_cast<uint64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+  uint64_t i = i0 + item * W + lane;  // this lane's edge in `item`
+  // slot of edge i in tgt (wraps below zero for the edges before the range: never used)
+  uint64_t at = 2 * (g.out_edge + i - g.begin);
+  const uint64_t at_step = 2 * step;
+  // Only the range's first node can start before the range (so only in item 0); later
+  // items are read straight from the output.
+  uint64_t t_next = 0;
+  if (item < items && lane < W && i < g.end)
+    t_next = i >= g.begin ? static_cast<uint64_t>(__ldcs(tgt + at))
+                          : array_value<RT, HasSeed>(draw(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
+  for (; item < items; item += warps, i += step, at += at_step) {
+    const uint64_t t = t_next;
+    if (lane < W && i + step < g.end)  // the next item's load in flight
+      t_next = static_cast<uint64_t>(__ldcs(tgt + (at + at_step)));
+    const bool part = lane < W && i < g.end;  // the edge matters to its node
+    // Does another edge of the node have the same target?  Lane j compares its key (low
+    // 32 bits) with the keys d/2 places after it, cyclically within the node, so every
+    // pair is compared once; a key equal to the empty marker raises the flag too.  A false
+    // alarm only sends the node through the exact pass below.  (__match_any_sync
+    // serialises over the distinct values of the warp; a hash table with shared-memory
+    // atomicCAS and a count over the whole row were slower than this.)
+    const uint32_t key = static_cast<uint32_t>(t);
+    __syncwarp();
+    if (lane < W) row[0] = row[d] = part ? key : kNoKey;
+    __syncwarp();
+    // every pair of the node's edges is some lane's offset o <= d/2 (or d - o)
+    bool seen = key == kNoKey;
+    if (lane < W) {
+#pragma unroll 4
+      for (uint32_t o = 1; o <= half; ++o) seen |= row[o] == key;
+    }
+    uint32_t dups = __ballot_sync(kAll, part && seen);
     if (dups == 0) continue;
+    // Exact pass, node by node, edges in order: an edge whose candidate one of the node's
+    // earlier edges has accepted draws again while a new target exists and redraws are left.
     const uint32_t parts = __ballot_sync(kAll, part);
     uint64_t acc = t;
-    while (dups) {  // nodes with a duplicate, one at a time, edges in order
-      const uint32_t first = __ffs(dups) - 1;
-      const uint32_t base = (first / d) * d;
+    while (dups) {
+      const uint32_t base = ((__ffs(dups) - 1) / d) * d;
       const uint32_t node_lanes = (d == 32 ? kAll : ((1u << d) - 1u)) << base;
-      const uint64_t reach_l = __shfl_sync(kAll, reach, first);
-      for (uint32_t L = first; L < base + d && ((parts >> L) & 1u); ++L) {
-        const uint64_t iL = __shfl_sync(kAll, i, L);
+      const uint64_t node = g.n0 + q_lo + item * npw + base / d;
+      const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
+      for (uint32_t L = base + 1; L < base + d && ((parts >> L) & 1u); ++L) {
+        const uint64_t iL = i - lane + L;
         uint64_t cand = __shfl_sync(kAll, acc, L);
         uint32_t k = 0;
         for (;;) {
           const bool taken = __ballot_sync(kAll, lane >= base && lane < L && acc == cand) != 0;
-          if (!taken || L - base >= reach_l || k >= kRedrawCap) break;
+          if (!taken || L - base >= reach || k >= kRedrawCap) break;
           ++k;
           uint64_t v = 0;
           if (lane == L) v = redraw<RT, HasSeed>(iL, k, g, draw, l2m0);
@@ -102,7 +135,7 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, 
       }
       dups &= ~node_lanes;
     }
-    if (in_out && acc != t) __stcs(dst, static_cast<long long>(acc));
+    if (part && i >= g.begin && acc != t) __stcs(tgt + at, static_cast<long long>(acc));
   }
 }
 
@@ -110,7 +143,7 @@ template <class RT, bool HasSeed, class Draw, bool NoLoop>
 ba_status launch_t(const GraphDev &g, int64_t *out, uint64_t q_lo, uint64_t q_hi, uint32_t npw,
                    cudaStream_t stream) {
   auto kernel = k_reject_duplicates<RT, HasSeed, Draw, NoLoop>;
-  constexpr int kBlock = 256;
+  constexpr int kBlock = kThreads;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
