@@ -47,6 +47,7 @@ __device__ __noinline__ uint64_t redraw(uint64_t i, uint32_t k, const GraphDev &
 }
 
 constexpr int kThreads = 256;
+constexpr int kGroup = 4;  // items per pass of a warp's loop
 constexpr uint32_t kNoKey = 0xffffffffu;
 
 // Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]: the W = npw * d edges
@@ -73,69 +74,80 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, 
   const uint32_t half = d / 2;
   const uint64_t i0 = g.m0 + q_lo * d;
   const uint64_t items = (q_hi - q_lo) / npw + 1;
+  const uint64_t groups = (items + kGroup - 1) / kGroup;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kThreads / 32);
-  const uint64_t step = warps * W;  // edges between a warp's consecutive items
   long long *const tgt = reinterpret_cast<long long *>(out) + 1;  // targets: stride 2
-  uint64_t item = static_cast<uint64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-  uint64_t i = i0 + item * W + lane;  // this lane's edge in `item`
-  // slot of edge i in tgt (wraps below zero for the edges before the range: never used)
-  uint64_t at = 2 * (g.out_edge + i - g.begin);
-  const uint64_t at_step = 2 * step;
-  // Only the range's first node can start before the range (so only in item 0); later
-  // items are read straight from the output.
-  uint64_t t_next = 0;
-  if (item < items && lane < W && i < g.end)
-    t_next = i >= g.begin ? static_cast<uint64_t>(__ldcs(tgt + at))
-                          : array_value<RT, HasSeed>(draw(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
-  for (; item < items; item += warps, i += step, at += at_step) {
-    const uint64_t t = t_next;
-    if (lane < W && i + step < g.end)  // the next item's load in flight
-      t_next = static_cast<uint64_t>(__ldcs(tgt + (at + at_step)));
-    const bool part = lane < W && i < g.end;  // the edge matters to its node
+  for (uint64_t grp = static_cast<uint64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+       grp < groups; grp += warps) {
+    // kGroup consecutive items per pass of the loop: their loads in flight together
+    const uint64_t ib = i0 + grp * (kGroup * W) + lane;  // this lane's edge in the first
+    uint64_t t[kGroup];
+#pragma unroll
+    for (int k = 0; k < kGroup; ++k) {
+      const uint64_t ik = ib + k * W;
+      t[k] = 0;
+      if (lane < W && ik < g.end)  // only the range's first node can start before it
+        t[k] = ik >= g.begin ? static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (ik - g.begin))))
+                             : array_value<RT, HasSeed>(draw(static_cast<RT>(2 * ik + 1)), g, draw,
+                                                        l2m0);
+    }
     // Does another edge of the node have the same target?  Lane j compares its key (low
     // 32 bits) with the keys d/2 places after it, cyclically within the node, so every
     // pair is compared once; a key equal to the empty marker raises the flag too.  A false
     // alarm only sends the node through the exact pass below.  (__match_any_sync
     // serialises over the distinct values of the warp; a hash table with shared-memory
     // atomicCAS and a count over the whole row were slower than this.)
-    const uint32_t key = static_cast<uint32_t>(t);
-    __syncwarp();
-    if (lane < W) row[0] = row[d] = part ? key : kNoKey;
-    __syncwarp();
-    // every pair of the node's edges is some lane's offset o <= d/2 (or d - o)
-    bool seen = key == kNoKey;
-    if (lane < W) {
+    uint32_t flags = 0;
+#pragma unroll
+    for (int k = 0; k < kGroup; ++k) {
+      const bool part = lane < W && ib + k * W < g.end;  // the edge matters to its node
+      const uint32_t key = static_cast<uint32_t>(t[k]);
+      __syncwarp();
+      if (lane < W) row[0] = row[d] = part ? key : kNoKey;
+      __syncwarp();
+      bool seen = key == kNoKey;
+      if (lane < W) {
 #pragma unroll 4
-      for (uint32_t o = 1; o <= half; ++o) seen |= row[o] == key;
+        for (uint32_t o = 1; o <= half; ++o) seen |= row[o] == key;
+      }
+      flags |= (part && seen) ? 1u << k : 0u;
     }
-    uint32_t dups = __ballot_sync(kAll, part && seen);
-    if (dups == 0) continue;
+    if (__ballot_sync(kAll, flags != 0) == 0) continue;
     // Exact pass, node by node, edges in order: an edge whose candidate one of the node's
     // earlier edges has accepted draws again while a new target exists and redraws are left.
-    const uint32_t parts = __ballot_sync(kAll, part);
-    uint64_t acc = t;
-    while (dups) {
-      const uint32_t base = ((__ffs(dups) - 1) / d) * d;
-      const uint32_t node_lanes = (d == 32 ? kAll : ((1u << d) - 1u)) << base;
-      const uint64_t node = g.n0 + q_lo + item * npw + base / d;
-      const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
-      for (uint32_t L = base + 1; L < base + d && ((parts >> L) & 1u); ++L) {
-        const uint64_t iL = i - lane + L;
-        uint64_t cand = __shfl_sync(kAll, acc, L);
-        uint32_t k = 0;
-        for (;;) {
-          const bool taken = __ballot_sync(kAll, lane >= base && lane < L && acc == cand) != 0;
-          if (!taken || L - base >= reach || k >= kRedrawCap) break;
-          ++k;
-          uint64_t v = 0;
-          if (lane == L) v = redraw<RT, HasSeed>(iL, k, g, draw, l2m0);
-          cand = __shfl_sync(kAll, v, L);
+#pragma unroll 1
+    for (int k = 0; k < kGroup; ++k) {
+      uint32_t dups = __ballot_sync(kAll, (flags >> k) & 1u);
+      if (dups == 0) continue;
+      const uint64_t i = ib + k * W;
+      const bool part = lane < W && i < g.end;
+      const uint32_t parts = __ballot_sync(kAll, part);
+      const uint64_t t_k = k == 0 ? t[0] : k == 1 ? t[1] : k == 2 ? t[2] : t[3];
+      uint64_t acc = t_k;
+      while (dups) {
+        const uint32_t base = ((__ffs(dups) - 1) / d) * d;
+        const uint32_t node_lanes = (d == 32 ? kAll : ((1u << d) - 1u)) << base;
+        const uint64_t node = g.n0 + q_lo + (grp * kGroup + k) * npw + base / d;
+        const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
+        for (uint32_t L = base + 1; L < base + d && ((parts >> L) & 1u); ++L) {
+          const uint64_t iL = i - lane + L;
+          uint64_t cand = __shfl_sync(kAll, acc, L);
+          uint32_t r = 0;
+          for (;;) {
+            const bool taken = __ballot_sync(kAll, lane >= base && lane < L && acc == cand) != 0;
+            if (!taken || L - base >= reach || r >= kRedrawCap) break;
+            ++r;
+            uint64_t v = 0;
+            if (lane == L) v = redraw<RT, HasSeed>(iL, r, g, draw, l2m0);
+            cand = __shfl_sync(kAll, v, L);
+          }
+          if (lane == L) acc = cand;
         }
-        if (lane == L) acc = cand;
+        dups &= ~node_lanes;
       }
-      dups &= ~node_lanes;
+      if (part && i >= g.begin && acc != t_k)
+        __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(acc));
     }
-    if (part && i >= g.begin && acc != t) __stcs(tgt + at, static_cast<long long>(acc));
   }
 }
 
@@ -148,7 +160,8 @@ ba_status launch_t(const GraphDev &g, int64_t *out, uint64_t q_lo, uint64_t q_hi
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   const uint64_t items = (q_hi - q_lo) / npw + 1;
-  const uint64_t want = (items + kBlock / 32 - 1) / (kBlock / 32);
+  const uint64_t groups = (items + kGroup - 1) / kGroup;
+  const uint64_t want = (groups + kBlock / 32 - 1) / (kBlock / 32);
   const int grid = static_cast<int>(std::min<uint64_t>(
       want, static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(std::max(per_sm, 1))));
   kernel<<<grid, kBlock, 0, stream>>>(g, out, q_lo, q_hi, npw);
