@@ -5,16 +5,17 @@
 // the target of the array without rejection (the array every chain follows: the
 // recursion of Fig. 1 cannot see rejections made while another node was generated).
 // k_reject_duplicates then walks the nodes that own edges in range, one lane per edge of a
-// node (d <= 32, so a warp holds 32/d whole nodes):
+// node (d <= 32, so an item of a warp holds 32/d whole nodes; a warp takes kGroup items
+// per pass, their loads in flight together):
 //   1. each lane holds its edge's target (read back from the output, or recomputed for
 //      the edges of the first node that lie before the range);
 //   2. each lane compares its target (low 32 bits) with those of the next d/2 edges of its
-//      node, cyclically, through shared memory; a warp without a repeat is done;
-//   3. otherwise the flagged nodes' edges are taken in order: while an
-//      edge's candidate is one of the targets accepted before it (a ballot over the node's
-//      lanes), j < reach(u) and fewer than kRedrawCap redraws were made, its lane redraws:
-//      the plain draw's range and key 2i+1 with the SplitMix64 bits of
-//      seed ^ k * kRedrawSalt, then the array's chain from the drawn position.
+//      node, cyclically, through shared memory; a pass without a repeat is done;
+//   3. otherwise the flagged nodes' edges are taken in order: while an edge's candidate
+//      is one of the targets accepted before it (a ballot over the node's lanes),
+//      j < reach(u) and fewer than kRedrawCap redraws were made, its lane redraws: the
+//      plain draw's range and key 2i+1 with the SplitMix64 bits of seed ^ k * kRedrawSalt,
+//      then the array's chain from the drawn position.
 // Only changed targets are written back.  Sources and seed-clique edges never change.
 #include <algorithm>
 
