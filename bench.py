@@ -11,7 +11,9 @@ summed across ranks.
 
 Extra keys: the streaming-only workload (n = 10^10, d = 100, 10^12 edges), the batched
 launch over the first wave of the 4096-graph table, the serving loop under Poisson
-arrivals, and the small workload (n = 10^6, d = 4).
+arrivals, the small workload (n = 10^6, d = 4), the int32 output, and the variant graphs
+(Fig. 3's hash_crc, section 4's self-loop-free rule and its rejection of parallel edges)
+on the large workload's shape.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 """
