@@ -634,6 +634,17 @@ def variants(ba, torch, stream, main):
             res[name]["reject_pass_read_gbs"] = 16 * m / (pass_ms * 1e6) if pass_ms > 0 else None
     del out
     torch.cuda.empty_cache()
+    counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
+    m = gl.m
+    call = lambda: ba.ba_degree_count_variant(gl.seed, gl.n, gl.d, 0, 0, m, NODE_LIMIT, P, counts,
+                                              0, stream)
+    call()
+    t = statistics.median(_time_events(call, stream, torch, 3))
+    plain_deg_ms = main["kernels_ms"]["degree"]
+    res["no_parallel_edges_degree"] = {
+        "workload": f"n=2^27 d=16 n0=0 seed=42 without parallel edges, degree count of nodes "
+                    f"< 1e5 over all {m} edges (the array's count, then every node recomputed)",
+        "edges_per_s": m / t, "ms": 1e3 * t, "vs_plain_degree": plain_deg_ms / (1e3 * t)}
     g = W.STREAM_HUGE
     b = g.m // 10
     counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")

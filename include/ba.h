@@ -154,8 +154,9 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
  *                            n0 = 1 or NO_SELF_LOOPS) and for at most 65536 redraws.
  *                            Chains follow the array without rejection, so only the
  *                            node's own output changes.  Needs d <= 32; combines with
- *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH;
- *                            generation only (ba_degree_count_variant rejects it).
+ *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  In a
+ *                            degree count every node's targets are recomputed (a second
+ *                            chain pass after the count of the array's own targets).
  * The flags combine as stated.  Unknown flags, NO_SELF_LOOPS with n0 < 2, or
  * NO_PARALLEL_EDGES outside its limits give BA_ERR_INVALID_ARG. */
 #define BA_VARIANT_CRC_HASH 1u

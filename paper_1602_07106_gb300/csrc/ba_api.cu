@@ -341,10 +341,6 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
   if (st != BA_OK) return st;
   st = check_variant(variant, d, n0);
   if (st != BA_OK) return st;
-  if (variant & BA_VARIANT_NO_PARALLEL_EDGES) {
-    set_error("degree counts of the graph without parallel edges are not supported");
-    return BA_ERR_INVALID_ARG;
-  }
   if (node_limit == 0) return BA_OK;
   if (counts_dev == nullptr || (reinterpret_cast<uintptr_t>(counts_dev) & 7) != 0) {
     set_error("counts must be a non-NULL, 8-byte aligned device pointer");
@@ -361,8 +357,12 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
   StreamScratch scratch;
   st = scratch.alloc(sizeof(unsigned long long), s);
   if (st != BA_OK) return st;
-  return launch_degree_variant(g, node_limit, counts_dev, accumulate, shape,
-                               static_cast<unsigned long long *>(scratch.ptr), s, variant);
+  const uint32_t draw_flags = variant & (BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS);
+  st = launch_degree_variant(g, node_limit, counts_dev, accumulate, shape,
+                             static_cast<unsigned long long *>(scratch.ptr), s, draw_flags);
+  if (st != BA_OK || !(variant & BA_VARIANT_NO_PARALLEL_EDGES)) return st;
+  return launch_count_rejections(g, node_limit, counts_dev, s,
+                                 (variant & BA_VARIANT_NO_SELF_LOOPS) != 0);
 }
 
 ba_status ba_generate_edges_host(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,

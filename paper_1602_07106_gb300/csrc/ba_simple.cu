@@ -53,10 +53,14 @@ constexpr uint32_t kNoKey = 0xffffffffu;
 
 // Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]: the W = npw * d edges
 // i0 + item * W + lane (lane < W), i0 = the first edge of node n0 + q_lo; lane = slot*d + j.
-template <class RT, bool HasSeed, class Draw, bool NoLoop>
+// Count: nothing is stored (section 3's streaming analysis): every target is recomputed by
+// its chain, and a changed edge moves one count from its old target to its new one
+// (counts below node_limit only) instead of being written.
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
 __global__ void __launch_bounds__(kThreads)
-k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, uint64_t q_hi,
-                    uint32_t npw) {
+k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
+                    unsigned long long *__restrict__ counts, uint64_t node_limit, uint64_t q_lo,
+                    uint64_t q_hi, uint32_t npw) {
   // per warp: the low 32 bits of each node's targets, written twice in a row (entries j
   // and j + d) so that lane j reads entry j + o for every offset o without a wrap; node s's
   // row starts at word s * (d + 64), so the lanes of one read hit distinct banks (d >= 2:
@@ -87,10 +91,12 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, 
     for (int k = 0; k < kGroup; ++k) {
       const uint64_t ik = ib + k * W;
       t[k] = 0;
-      if (lane < W && ik < g.end)  // only the range's first node can start before it
-        t[k] = ik >= g.begin ? static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (ik - g.begin))))
-                             : array_value<RT, HasSeed>(draw(static_cast<RT>(2 * ik + 1)), g, draw,
-                                                        l2m0);
+      if (lane < W && ik < g.end) {  // only the range's first node can start before it
+        if (!Count && ik >= g.begin)
+          t[k] = static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (ik - g.begin))));
+        else
+          t[k] = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * ik + 1)), g, draw, l2m0);
+      }
     }
     // Does another edge of the node have the same target?  Lane j compares its key (low
     // 32 bits) with the keys d/2 places after it, cyclically within the node, so every
@@ -146,16 +152,23 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out, uint64_t q_lo, 
         }
         dups &= ~node_lanes;
       }
-      if (part && i >= g.begin && acc != t_k)
-        __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(acc));
+      if (part && i >= g.begin && acc != t_k) {
+        if constexpr (Count) {
+          if (t_k < node_limit) atomicAdd(counts + t_k, ~0ull);  // minus one, mod 2^64
+          if (acc < node_limit) atomicAdd(counts + acc, 1ull);
+        } else {
+          __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(acc));
+        }
+      }
     }
   }
 }
 
-template <class RT, bool HasSeed, class Draw, bool NoLoop>
-ba_status launch_t(const GraphDev &g, int64_t *out, uint64_t q_lo, uint64_t q_hi, uint32_t npw,
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
+ba_status launch_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
+                   uint64_t node_limit, uint64_t q_lo, uint64_t q_hi, uint32_t npw,
                    cudaStream_t stream) {
-  auto kernel = k_reject_duplicates<RT, HasSeed, Draw, NoLoop>;
+  auto kernel = k_reject_duplicates<RT, HasSeed, Draw, NoLoop, Count>;
   constexpr int kBlock = kThreads;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
@@ -165,15 +178,15 @@ ba_status launch_t(const GraphDev &g, int64_t *out, uint64_t q_lo, uint64_t q_hi
   const uint64_t want = (groups + kBlock / 32 - 1) / (kBlock / 32);
   const int grid = static_cast<int>(std::min<uint64_t>(
       want, static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(std::max(per_sm, 1))));
-  kernel<<<grid, kBlock, 0, stream>>>(g, out, q_lo, q_hi, npw);
+  kernel<<<grid, kBlock, 0, stream>>>(g, out, counts, node_limit, q_lo, q_hi, npw);
   e = cudaGetLastError();
   return e == cudaSuccess ? BA_OK : cuda_fail(e, "k_reject_duplicates");
 }
 
-}  // namespace
-
-ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
-                                   bool no_loops) {
+// The nodes with edges in [g.begin, g.end), then the launch for the draw family.
+template <bool Count>
+ba_status reject_range(const GraphDev &g, int64_t *out, unsigned long long *counts,
+                       uint64_t node_limit, cudaStream_t stream, bool no_loops) {
   if (g.d <= 1 || g.d > 32) return g.d <= 1 ? BA_OK : BA_ERR_INVALID_ARG;
   const uint64_t a = std::max(g.begin, g.m0);
   if (a >= g.end) return BA_OK;  // only seed-clique edges in range
@@ -183,14 +196,27 @@ ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t
   const bool r32 = g.end <= (1ull << 31);
   if (no_loops) {  // needs a seed edge, so a seed clique
     using D = DrawVariant<false, true>;
-    return r32 ? launch_t<uint32_t, true, D, true>(g, out, q_lo, q_hi, npw, stream)
-               : launch_t<uint64_t, true, D, true>(g, out, q_lo, q_hi, npw, stream);
+    return r32 ? launch_t<uint32_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream)
+               : launch_t<uint64_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream);
   }
   if (g.m0 > 0)
-    return r32 ? launch_t<uint32_t, true, DrawPlain, false>(g, out, q_lo, q_hi, npw, stream)
-               : launch_t<uint64_t, true, DrawPlain, false>(g, out, q_lo, q_hi, npw, stream);
-  return r32 ? launch_t<uint32_t, false, DrawPlain, false>(g, out, q_lo, q_hi, npw, stream)
-             : launch_t<uint64_t, false, DrawPlain, false>(g, out, q_lo, q_hi, npw, stream);
+    return r32 ? launch_t<uint32_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream)
+               : launch_t<uint64_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream);
+  return r32 ? launch_t<uint32_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream)
+             : launch_t<uint64_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream);
+}
+
+}  // namespace
+
+ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
+                                   bool no_loops) {
+  return reject_range<false>(g, out, nullptr, 0, stream, no_loops);
+}
+
+ba_status launch_count_rejections(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                                  cudaStream_t stream, bool no_loops) {
+  return reject_range<true>(g, nullptr, reinterpret_cast<unsigned long long *>(counts), node_limit,
+                            stream, no_loops);
 }
 
 }  // namespace ba

@@ -1,8 +1,9 @@
 """GPU parity of the graph without parallel edges (BA_VARIANT_NO_PARALLEL_EDGES, section 4:
 a node's duplicate targets are rejected and redrawn) against the oracle, bit-exact: whole
 graphs, ranges that start or end inside a node, both position paths, with and without
-self-loops and seed cliques, d up to 32, and the 2^31-edge graph at full size on sampled
-ranges plus the no-parallel-edge property over every node."""
+self-loops and seed cliques, d up to 32, the 2^31-edge graph at full size on sampled
+ranges plus the no-parallel-edge property over every node, and the streaming degree count
+of the same graph."""
 import numpy as np
 import pytest
 import torch
@@ -100,3 +101,32 @@ def test_full_size_graph(ba, no_loops, n0):
     ba.ba_generate_edges_variant(g.seed, g.n, g.d, n0, 0, m, v & ~SIMPLE, plain)
     changed = int((plain[:, 1] != out[:, 1]).sum())
     assert 0 < changed < m // 1000
+
+
+@pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", CASES)
+def test_degree_count_bit_exact_against_oracle(ba, seed, n, d, n0, no_loops, a, b):
+    m = oracle.num_edges(n, d, n0)
+    b = m if b is None else (m + b if b < 0 else b)
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    limit = min(n, 5_000) + 3
+    want = oracle.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+    counts = torch.full((limit,), 7, dtype=torch.int64, device="cuda")
+    ba.ba_degree_count_variant(seed, n, d, n0, a, b, limit, v, counts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
+    # a split of the range accumulates to the same counts
+    mid = (a + b) // 2 + 3
+    ba.ba_degree_count_variant(seed, n, d, n0, a, mid, limit, v, counts)
+    ba.ba_degree_count_variant(seed, n, d, n0, mid, b, limit, v, counts, accumulate=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
+
+
+def test_degree_count_64bit_positions(ba):
+    seed, n, d = 78, 2**29, 16
+    a, b = 2**33 - 200_000, 2**33
+    want = oracle.degree_count_range_simple(seed, n, d, 0, False, a, b, 100_000)
+    counts = torch.empty(100_000, dtype=torch.int64, device="cuda")
+    ba.ba_degree_count_variant(seed, n, d, 0, a, b, 100_000, SIMPLE, counts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
