@@ -112,3 +112,21 @@ def edges_range_simple(seed, n, d, n0, no_loops, a, b, workers: int | None = Non
     with mp.get_context("spawn").Pool(workers) as pool:
         parts = pool.map(_simple_edges_piece, jobs)
     return np.concatenate(parts, axis=0)
+
+
+def _simple_degrees_piece(args):
+    seed, n, d, n0, no_loops, a, b, limit = args
+    return oracle.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+
+
+def degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit,
+                              workers: int | None = None) -> np.ndarray:
+    """oracle.degree_count_range_simple over [a, b), split across processes and summed."""
+    workers = workers or default_workers()
+    if workers == 1 or b - a < 4_000_000:
+        return oracle.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+    oracle.build()
+    jobs = [(seed, n, d, n0, no_loops, x, y, limit) for x, y in _cuts(a, b, 4 * workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_simple_degrees_piece, jobs)
+    return np.sum(parts, axis=0, dtype=np.uint64)
