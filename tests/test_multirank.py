@@ -1,6 +1,8 @@
 """The N > 1 path on CPU: two gloo ranks shard a graph by edge ranges (no exchange), sum their
 degree counters with one all-reduce, and together reproduce the unsharded oracle bit for bit
-(paper section 2: the result does not depend on the number of processors)."""
+(paper section 2: the result does not depend on the number of processors) -- for the plain
+graph and for the simple graph of section 4 (no self-loops, duplicate targets rejected),
+whose shards cut through a node's edges."""
 import os
 import socket
 
@@ -23,7 +25,21 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, result_dir, weak):
+def _edges(simple, a, b):
+    seed, n, d, n0 = GRAPH
+    if simple:
+        return oracle.edges_range_simple(seed, n, d, n0, True, a, b)
+    return oracle.edges_range(seed, n, d, n0, a, b)
+
+
+def _counts(simple, a, b):
+    seed, n, d, n0 = GRAPH
+    if simple:
+        return oracle.degree_count_range_simple(seed, n, d, n0, True, a, b, LIMIT)
+    return oracle.degree_count_range(seed, n, d, n0, a, b, LIMIT)
+
+
+def _rank_main(rank, world, port, result_dir, weak, simple):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -33,8 +49,8 @@ def _rank_main(rank, world, port, result_dir, weak):
         a, b = shard.weak_shard(per, rank)
     else:
         a, b = shard.strong_shard(oracle.num_edges(n, d, n0), rank, world)
-    edges = torch.from_numpy(oracle.edges_range(seed, n, d, n0, a, b))
-    counts = torch.from_numpy(oracle.degree_count_range(seed, n, d, n0, a, b, LIMIT).astype(np.int64))
+    edges = torch.from_numpy(_edges(simple, a, b))
+    counts = torch.from_numpy(_counts(simple, a, b).astype(np.int64))
     shard.sum_degree_counts(counts)
     sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
     dist.all_gather(sizes, torch.tensor([edges.shape[0]]))
@@ -50,17 +66,19 @@ def _rank_main(rank, world, port, result_dir, weak):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("weak", [False, True])
-def test_two_gloo_ranks_reproduce_the_unsharded_graph(tmp_path, weak):
+@pytest.mark.parametrize("weak,simple", [(False, False), (True, False), (False, True)])
+def test_two_gloo_ranks_reproduce_the_unsharded_graph(tmp_path, weak, simple):
     world = 2
-    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path), weak), nprocs=world,
-                       join=True, start_method="spawn")
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path), weak, simple),
+                       nprocs=world, join=True, start_method="spawn")
     res = torch.load(tmp_path / "out.pt")
-    seed, n, d, n0 = GRAPH
     total = res["end"]
-    np.testing.assert_array_equal(res["edges"].numpy(), oracle.edges_range(seed, n, d, n0, 0, total))
+    np.testing.assert_array_equal(res["edges"].numpy(), _edges(simple, 0, total))
     np.testing.assert_array_equal(res["counts"].numpy().astype(np.uint64),
-                                  oracle.degree_count_range(seed, n, d, n0, 0, total, LIMIT))
+                                  _counts(simple, 0, total))
+    if simple:  # the cut falls inside a node
+        seed, n, d, n0 = GRAPH
+        assert (total // 2 - n0 * (n0 - 1) // 2) % d != 0
 
 
 def test_shard_bounds():
