@@ -185,13 +185,17 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
  *  tile         edges per warp tile (power of two, 64..2^20); plain calls halve it,
  *               down to 256, until every warp of the grid gets several tiles
  *  refill       0 = one thread per edge, no refill (the simple kernel);
- *               1 = warp refill every hash step (ballot/popc compaction)
+ *               1 = warp refill every hash step (ballot/popc compaction);
+ *               2 = lane chunks (degree count only): each lane walks its own run of
+ *                   consecutive edge IDs, no per-step compaction
  *  hist_bins    degree kernel: shared-memory histogram bins per CTA
  *  hist_agg     degree kernel: 1 = one shared-memory atomic per distinct node per warp
  *               (__match_any_sync aggregation), 0 = one atomic per hitting lane
  *  chains       refill kernels: hash chains each lane keeps in flight (1 or 2); a
  *               second independent chain hides the latency of the hash's dependent
- *               multiplies */
+ *               multiplies
+ *  lane_chunk   refill = 2 degree count: edges per lane chunk (power of two 32..1024,
+ *               0 = default) */
 typedef struct ba_tuning {
     int32_t block;
     int32_t ctas_per_sm;
@@ -200,7 +204,7 @@ typedef struct ba_tuning {
     int32_t hist_bins;
     int32_t hist_agg;
     int32_t chains;
-    int32_t reserved;
+    int32_t lane_chunk;
 } ba_tuning;
 
 /* Kernel families the tuner keys on. */
@@ -307,6 +311,30 @@ ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
 ba_status ba_generate_batch_noalloc(const ba_graph_desc *descs, int32_t G,
                                     const int64_t *offsets_host, int64_t *out_dev,
                                     void *stream);
+
+/* ---------------------------------------------------------------- roofline probes -- */
+
+/*
+ * Integer floor of the hash chain (section 2's work bound: about two draws per edge).
+ * Runs `edges` units of exactly two draws h(r) each -- r = 2(base+e)+1, then the result
+ * made odd -- with no stop test, scheduling or stores, `chains` (1, 2 or 4) independent
+ * chains per thread, on a full grid.  base + edges <= 2^31 takes the 32-bit-position hash
+ * (the one plain calls with edge_end <= 2^31 use), larger bases the 64-bit one.  The XOR
+ * of all results is XORed into *sink_dev (device, 8 bytes, caller-owned) so that nothing
+ * is optimised away; its value has no other meaning.  Asynchronous on `stream`.
+ * Errors: BA_ERR_INVALID_ARG (NULL or misaligned sink, chains not 1/2/4), BA_ERR_RANGE
+ * (base + edges >= 2^60), BA_ERR_CUDA.
+ */
+ba_status ba_probe_hash(uint64_t seed, uint64_t base, uint64_t edges, int32_t chains,
+                        uint64_t *sink_dev, void *stream);
+
+/*
+ * HBM write bandwidth: 16-byte streaming stores (the generate kernels' store) over
+ * dst_dev[0 .. bytes), nothing read; the contents afterwards are unspecified.  dst_dev
+ * (device, caller-owned) 16-byte aligned, bytes a multiple of 16, else BA_ERR_INVALID_ARG.
+ * Asynchronous on `stream`.
+ */
+ba_status ba_probe_write(void *dst_dev, uint64_t bytes, void *stream);
 
 /* ------------------------------------------------- serving (continuous batching) -- */
 

@@ -36,12 +36,12 @@ _vp = ctypes.c_void_p
 class ba_tuning(ctypes.Structure):
     _fields_ = [("block", _i32), ("ctas_per_sm", _i32), ("tile", _i32), ("refill", _i32),
                 ("hist_bins", _i32), ("hist_agg", _i32), ("chains", _i32),
-                ("reserved", _i32)]
+                ("lane_chunk", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k)
                 for k in ("block", "ctas_per_sm", "tile", "refill", "hist_bins", "hist_agg",
-                          "chains")}
+                          "chains", "lane_chunk")}
 
 
 class ba_graph_desc(ctypes.Structure):
@@ -97,6 +97,8 @@ _sig("ba_generate_batch", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp
      ctypes.POINTER(ba_tuning), _vp)
 _sig("ba_generate_batch_noalloc", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp, _vp,
      _vp)
+_sig("ba_probe_hash", ctypes.c_int, _u64, _u64, _u64, _i32, _vp, _vp)
+_sig("ba_probe_write", ctypes.c_int, _vp, _u64, _vp)
 _sig("ba_server_create", ctypes.c_int, ctypes.POINTER(ba_server_config), ctypes.POINTER(_vp))
 _sig("ba_server_submit", ctypes.c_int, _vp, ctypes.POINTER(ba_graph_desc), ctypes.POINTER(_u64))
 _sig("ba_server_poll", ctypes.c_int, _vp, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_u64))
@@ -315,6 +317,19 @@ def ba_generate_batch_noalloc(graphs, out, offsets=None, stream=None) -> None:
     keep, off = _offsets_arg(offsets)
     _check(_lib.ba_generate_batch_noalloc(arr, G, off, _ptr(out), _stream(stream)),
            "ba_generate_batch_noalloc")
+
+
+def ba_probe_hash(seed, base, edges, chains, sink, stream=None) -> None:
+    """Two draws per edge with nothing else (the integer floor of the chain); sink is a
+    one-element int64 device tensor that receives an XOR of the results."""
+    _check(_lib.ba_probe_hash(seed, base, edges, chains, _ptr(sink), _stream(stream)),
+           "ba_probe_hash")
+
+
+def ba_probe_write(dst, nbytes=None, stream=None) -> None:
+    """16-byte streaming stores over the device tensor dst (its first nbytes bytes)."""
+    n = dst.numel() * dst.element_size() if nbytes is None else nbytes
+    _check(_lib.ba_probe_write(_ptr(dst), n, _stream(stream)), "ba_probe_write")
 
 
 def ba_server_create(memory_budget_bytes=0, chunk_edges=0, max_active=0, max_inflight_ticks=0,

@@ -133,6 +133,42 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
         ba.ba_tune_load(str(tmp_path / "missing.json"))
 
 
+def test_lane_chunk_shapes_are_degree_only():
+    # refill 2 (lane chunks) exists for the degree count only; its chunk is a power of two
+    for kind in (ba.BA_KIND_GENERATE, ba.BA_KIND_BATCH):
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_set_tuning(kind, {"refill": 2})
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+    for bad in ({"refill": 2, "lane_chunk": 48}, {"refill": 2, "lane_chunk": 16},
+                {"refill": 2, "lane_chunk": 2048}):
+        with pytest.raises(ba.BAError):
+            ba.ba_set_tuning(ba.BA_KIND_DEGREE, bad)
+    try:
+        ba.ba_set_tuning(ba.BA_KIND_DEGREE, {"refill": 2, "lane_chunk": 256, "chains": 1})
+        t = ba.ba_get_tuning(ba.BA_KIND_DEGREE)
+        assert (t["refill"], t["lane_chunk"], t["chains"]) == (2, 256, 1)
+    finally:
+        ba.ba_set_tuning(ba.BA_KIND_DEGREE, None)
+
+
+def test_probe_argument_rules():
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_probe_hash(1, 0, 100, 1, None, stream=0)                 # no sink
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_probe_hash(1, 0, 100, 3, 0x1000, stream=0)               # chains 3
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_probe_hash(1, 2**60, 100, 1, 0x1000, stream=0)           # past 2^60
+    assert e.value.status == ba.BA_ERR_RANGE
+    ba.ba_probe_hash(1, 0, 0, 1, 0x1000, stream=0)                     # nothing to do
+    for dst, n in ((0x1008, 64), (0x1000, 40), (None, 64)):
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_probe_write(dst, n, stream=0)
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+    ba.ba_probe_write(None, 0, stream=0)                               # nothing to do
+
+
 def test_batch_and_server_argument_rules():
     with pytest.raises(ba.BAError) as e:
         ba.ba_batch_plan_create([(1, 10, 0, 0, 0, 5)])                  # d = 0

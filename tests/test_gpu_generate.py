@@ -87,22 +87,43 @@ def test_output_does_not_depend_on_launch_shape(ba, shape):
         ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
 
 
-def test_64_bit_positions_far_into_a_large_graph(ba):
+SCHEDULERS = [None, {"refill": 1, "chains": 1},
+              {"refill": 1, "chains": 2, "block": 128, "tile": 256}]
+
+
+def _with_shape(ba, shape, fn):
+    try:
+        if shape is not None:
+            ba.ba_set_tuning(ba.BA_KIND_GENERATE, shape)
+        fn()
+    finally:
+        ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
+
+
+@pytest.mark.parametrize("shape", SCHEDULERS, ids=str)
+def test_64_bit_positions_far_into_a_large_graph(ba, shape):
     # m = 2^33: positions above 2^32 take the 64-bit path
     n, d = 2**29, 16
     m = n * d
-    for a, b in [(m - 300_000, m), (2**31 - 1000, 2**31 + 150_000), (2**32 - 777, 2**32 + 777)]:
-        np.testing.assert_array_equal(_gpu(ba, 77, n, d, 0, a, b),
-                                      opar.edges_range(77, n, d, 0, a, b))
+
+    def run():
+        for a, b in [(m - 300_000, m), (2**31 - 1000, 2**31 + 150_000), (2**32 - 777, 2**32 + 777)]:
+            np.testing.assert_array_equal(_gpu(ba, 77, n, d, 0, a, b),
+                                          opar.edges_range(77, n, d, 0, a, b))
+    _with_shape(ba, shape, run)
 
 
+@pytest.mark.parametrize("shape", SCHEDULERS, ids=str)
 @pytest.mark.parametrize("seed,n,d,n0", [(81, 2**29, 13, 0), (83, 2**28, 24, 25), (85, 2**29, 8, 9)])
-def test_64_bit_positions_other_d_and_seed_cliques(ba, seed, n, d, n0):
+def test_64_bit_positions_other_d_and_seed_cliques(ba, seed, n, d, n0, shape):
     # the 64-bit flush's general path (d not a power of two, or a seed clique)
     m = ba.ba_num_edges(n, d, n0)
-    for a, b in [(m - 200_000, m), (2**31 - 500, 2**31 + 60_000)]:
-        np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
-                                      opar.edges_range(seed, n, d, n0, a, b))
+
+    def run():
+        for a, b in [(m - 200_000, m), (2**31 - 500, 2**31 + 60_000)]:
+            np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b),
+                                          opar.edges_range(seed, n, d, n0, a, b))
+    _with_shape(ba, shape, run)
 
 
 def test_host_output_matches_device_output(ba):
