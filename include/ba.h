@@ -153,7 +153,7 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
  *                            as a new one exists (edge j < reach(u): u+1 nodes, u with
  *                            n0 = 1 or NO_SELF_LOOPS) and for at most 65536 redraws.
  *                            Chains follow the array without rejection, so only the
- *                            node's own output changes.  Needs d <= 32; combines with
+ *                            node's own output changes.  Needs d <= 1024; combines with
  *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  In a
  *                            degree count every node's targets are recomputed (a second
  *                            chain pass after the count of the array's own targets).

@@ -293,8 +293,8 @@ static ba_status check_variant(uint32_t variant, uint32_t d, uint64_t n0) {
     set_error("the self-loop-free graph needs a seed graph with an edge (n0 >= 2)");
     return BA_ERR_INVALID_ARG;
   }
-  if ((variant & BA_VARIANT_NO_PARALLEL_EDGES) && ((variant & BA_VARIANT_CRC_HASH) || d > 32)) {
-    set_error("rejecting parallel edges needs d <= 32 and the SplitMix64 hash");
+  if ((variant & BA_VARIANT_NO_PARALLEL_EDGES) && ((variant & BA_VARIANT_CRC_HASH) || d > 1024)) {
+    set_error("rejecting parallel edges needs d <= 1024 and the SplitMix64 hash");
     return BA_ERR_INVALID_ARG;
   }
   return BA_OK;

@@ -75,12 +75,12 @@ ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t
                                 int accumulate, const Shape &s, unsigned long long *counter,
                                 cudaStream_t stream, uint32_t variant);
 // Section 4's rejection of a node's duplicate targets over an output that the generate
-// kernel (plain, or self-loop-free with no_loops) has already written; d <= 32.
+// kernel (plain, or self-loop-free with no_loops) has already written; d <= 1024.
 ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
                                    bool no_loops);
 // The same rejections for a degree count: counts[] (below node_limit) already holds the
 // counts of the array's own targets for [g.begin, g.end); each changed edge moves one count
-// from its old target to its new one.  d <= 32.
+// from its old target to its new one.  d <= 1024.
 ba_status launch_count_rejections(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                                   cudaStream_t stream, bool no_loops);
 ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,

@@ -6,7 +6,8 @@
 // recursion of Fig. 1 cannot see rejections made while another node was generated).
 // k_reject_duplicates then walks the nodes that own edges in range, one lane per edge of a
 // node (d <= 32, so an item of a warp holds 32/d whole nodes; a warp takes kGroup items
-// per pass, their loads in flight together):
+// per pass, their loads in flight together; k_reject_duplicates_wide below takes nodes of
+// 33..1024 edges, one warp per node):
 //   1. each lane holds its edge's target (read back from the output, or recomputed for
 //      the edges of the first node that lie before the range);
 //   2. each lane compares its target (low 32 bits) with those of the next d/2 edges of its
@@ -164,6 +165,138 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
   }
 }
 
+// ---------------------------------------------------------------- wide nodes, d > 32 --
+//
+// One warp per node: the node's targets (read back, or recomputed for the edges of the
+// range's first node that lie before it, or for every edge when counting) go to the
+// warp's shared row 32 at a time, and each lane inserts the low 32 bits of its target
+// into the warp's open-addressing table (2d..4d slots, linear probing, atomicCAS).  A key
+// that is already there flags the node; a false alarm (equal low halves) only sends the
+// node through the exact pass, which takes the node's edges in order exactly as the
+// narrow kernel does: while an edge's candidate is among the targets accepted before it
+// (a warp-wide scan of the row), j < reach(u) and redraws are left, lane 0 redraws.
+constexpr int kWideThreads = 128;
+constexpr uint32_t kWideMaxD = 1024;
+
+__host__ __device__ constexpr uint32_t wide_table_bits(uint32_t d) {
+  uint32_t b = 6;  // at least 64 slots
+  while ((1u << b) < 2 * d) ++b;
+  return b;
+}
+__host__ __device__ constexpr size_t wide_warp_bytes(uint32_t d) {
+  return static_cast<size_t>(d) * 8 + (static_cast<size_t>(4) << wide_table_bits(d));
+}
+
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
+__global__ void __launch_bounds__(kWideThreads)
+k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
+                         unsigned long long *__restrict__ counts, uint64_t node_limit,
+                         uint64_t q_lo, uint64_t q_hi) {
+  extern __shared__ __align__(16) unsigned char wide_smem[];
+  const uint32_t d = g.d;
+  const uint32_t bits = wide_table_bits(d);
+  const uint32_t P = 1u << bits;
+  unsigned char *mine = wide_smem + static_cast<size_t>(threadIdx.x >> 5) * wide_warp_bytes(d);
+  uint64_t *tt = reinterpret_cast<uint64_t *>(mine);            // the node's targets, d
+  uint32_t *tab = reinterpret_cast<uint32_t *>(mine + static_cast<size_t>(d) * 8);  // P keys
+  Draw draw;
+  draw.setup(g, nullptr, sizeof(RT) == 4);
+  draw.bind(g);
+  const RT l2m0 = seed_limit<RT>(g.two_m0);
+  const uint32_t lane = threadIdx.x & 31;
+  long long *const tgt = reinterpret_cast<long long *>(out) + 1;  // targets: stride 2
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kWideThreads / 32);
+  for (uint64_t q = q_lo + static_cast<uint64_t>(blockIdx.x) * (kWideThreads / 32) + (threadIdx.x >> 5);
+       q <= q_hi; q += warps) {
+    const uint64_t node = g.n0 + q;
+    const uint64_t first = g.m0 + q * d;
+    const uint32_t cnt = static_cast<uint32_t>(min(static_cast<uint64_t>(d), g.end - first));
+    __syncwarp();  // the previous node's row and table are no longer read
+    for (uint32_t k = lane; k < P; k += 32) tab[k] = kNoKey;
+    __syncwarp();
+    bool dup = false;
+    for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      if (j < cnt) {
+        const uint64_t i = first + j;
+        uint64_t t;
+        if (!Count && i >= g.begin)
+          t = static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (i - g.begin))));
+        else
+          t = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
+        tt[j] = t;
+        const uint32_t key = static_cast<uint32_t>(t);
+        if (key == kNoKey) {
+          dup = true;  // the empty marker itself: leave it to the exact pass
+        } else {
+          uint32_t h = (key * 0x9E3779B1u) >> (32 - bits);
+          for (;;) {  // at most d keys in >= 2d slots: an empty slot always exists
+            const uint32_t old = atomicCAS(tab + h, kNoKey, key);
+            if (old == kNoKey) break;
+            if (old == key) {
+              dup = true;
+              break;
+            }
+            h = (h + 1) & (P - 1);
+          }
+        }
+      }
+    }
+    if (!__any_sync(kAll, dup)) continue;
+    __syncwarp();
+    const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
+    for (uint32_t j = 1; j < cnt; ++j) {
+      const uint64_t orig = tt[j];
+      uint64_t cand = orig;
+      uint32_t r = 0;
+      for (;;) {
+        bool taken = false;
+        for (uint32_t l = lane; l < j; l += 32) taken |= tt[l] == cand;
+        if (!__any_sync(kAll, taken) || j >= reach || r >= kRedrawCap) break;
+        ++r;
+        uint64_t v = 0;
+        if (lane == 0) v = redraw<RT, HasSeed>(first + j, r, g, draw, l2m0);
+        cand = __shfl_sync(kAll, v, 0);
+      }
+      if (cand != orig) {
+        const uint64_t i = first + j;
+        if (lane == 0) {
+          tt[j] = cand;
+          if (i >= g.begin) {
+            if constexpr (Count) {
+              if (orig < node_limit) atomicAdd(counts + orig, ~0ull);  // minus one, mod 2^64
+              if (cand < node_limit) atomicAdd(counts + cand, 1ull);
+            } else {
+              __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(cand));
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
+ba_status launch_wide_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
+                        uint64_t node_limit, uint64_t q_lo, uint64_t q_hi, cudaStream_t stream) {
+  auto kernel = k_reject_duplicates_wide<RT, HasSeed, Draw, NoLoop, Count>;
+  const size_t smem = (kWideThreads / 32) * wide_warp_bytes(g.d);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWideThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  const uint64_t nodes = q_hi - q_lo + 1;
+  const uint64_t want = (nodes + kWideThreads / 32 - 1) / (kWideThreads / 32);
+  const int grid = static_cast<int>(std::min<uint64_t>(
+      want, static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(std::max(per_sm, 1))));
+  kernel<<<grid, kWideThreads, smem, stream>>>(g, out, counts, node_limit, q_lo, q_hi);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? BA_OK : cuda_fail(e, "k_reject_duplicates_wide");
+}
+
 template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
 ba_status launch_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
                    uint64_t node_limit, uint64_t q_lo, uint64_t q_hi, uint32_t npw,
@@ -187,13 +320,25 @@ ba_status launch_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
 template <bool Count>
 ba_status reject_range(const GraphDev &g, int64_t *out, unsigned long long *counts,
                        uint64_t node_limit, cudaStream_t stream, bool no_loops) {
-  if (g.d <= 1 || g.d > 32) return g.d <= 1 ? BA_OK : BA_ERR_INVALID_ARG;
+  if (g.d <= 1 || g.d > kWideMaxD) return g.d <= 1 ? BA_OK : BA_ERR_INVALID_ARG;
   const uint64_t a = std::max(g.begin, g.m0);
   if (a >= g.end) return BA_OK;  // only seed-clique edges in range
   const uint64_t q_lo = (a - g.m0) / g.d;
   const uint64_t q_hi = (g.end - 1 - g.m0) / g.d;
-  const uint32_t npw = 32u / g.d;
   const bool r32 = g.end <= (1ull << 31);
+  if (g.d > 32) {  // one warp per node
+    if (no_loops) {
+      using D = DrawVariant<false, true>;
+      return r32 ? launch_wide_t<uint32_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, stream)
+                 : launch_wide_t<uint64_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, stream);
+    }
+    if (g.m0 > 0)
+      return r32 ? launch_wide_t<uint32_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, stream)
+                 : launch_wide_t<uint64_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, stream);
+    return r32 ? launch_wide_t<uint32_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, stream)
+               : launch_wide_t<uint64_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, stream);
+  }
+  const uint32_t npw = 32u / g.d;
   if (no_loops) {  // needs a seed edge, so a seed clique
     using D = DrawVariant<false, true>;
     return r32 ? launch_t<uint32_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream)

@@ -85,12 +85,12 @@ def test_variant_argument_rules():
         ba.ba_generate_edges_variant(1, 10, 2, 3, 0, 5, 8, out=0x1000, stream=0)
     assert e.value.status == ba.BA_ERR_INVALID_ARG
     P = ba.BA_VARIANT_NO_PARALLEL_EDGES
-    for d, v in ((33, P), (2, P | ba.BA_VARIANT_CRC_HASH)):   # d <= 32, SplitMix64 draws only
+    for d, v in ((1025, P), (2, P | ba.BA_VARIANT_CRC_HASH)):  # d <= 1024, SplitMix64 only
         with pytest.raises(ba.BAError) as e:
             ba.ba_generate_edges_variant(1, 10, d, 3, 0, 5, v, out=0x1000, stream=0)
         assert e.value.status == ba.BA_ERR_INVALID_ARG
     with pytest.raises(ba.BAError) as e:   # the same limits for a degree count
-        ba.ba_degree_count_variant(1, 10, 33, 3, 0, 5, 8, P, counts=0x1000, stream=0)
+        ba.ba_degree_count_variant(1, 10, 1025, 3, 0, 5, 8, P, counts=0x1000, stream=0)
     assert e.value.status == ba.BA_ERR_INVALID_ARG
     with pytest.raises(ba.BAError) as e:
         ba.ba_generate_edges_variant(1, 10, 2, 3, 0, 99, ba.BA_VARIANT_CRC_HASH, out=0x1000,

@@ -1,7 +1,8 @@
 """GPU parity of the graph without parallel edges (BA_VARIANT_NO_PARALLEL_EDGES, section 4:
 a node's duplicate targets are rejected and redrawn) against the oracle, bit-exact: whole
 graphs, ranges that start or end inside a node, both position paths, with and without
-self-loops and seed cliques, d up to 32, the 2^31-edge graph at full size on sampled
+self-loops and seed cliques, d up to 32 (a warp item of whole nodes) and 33..1024 (a warp
+per node), the 2^31-edge graph at full size on sampled
 ranges plus the no-parallel-edge property over every node, and the streaming degree count
 of the same graph."""
 import numpy as np
@@ -38,6 +39,66 @@ def test_bit_exact_against_oracle(ba, seed, n, d, n0, no_loops, a, b):
     v = SIMPLE | (NOLOOP if no_loops else 0)
     got = _gpu(ba, seed, n, d, n0, a, b, v)
     np.testing.assert_array_equal(got, oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b))
+
+
+# d > 32: one warp per node (the paper's m = 100n shape among them)
+WIDE_CASES = [(41, 3_000, 100, 0, False, 0, None), (42, 4_000, 33, 0, False, 17, -5),
+              (43, 2_500, 64, 65, True, 0, None), (44, 6_000, 100, 3, False, 1_234, 431_777),
+              (45, 1_200, 257, 1, False, 0, None), (46, 1_100, 1024, 0, False, 5_000, -700),
+              (47, 2_000, 100, 101, True, 99, -1), (2**63 + 9, 5_000, 48, 0, False, 0, None)]
+
+
+@pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", WIDE_CASES)
+def test_wide_nodes_bit_exact_against_oracle(ba, seed, n, d, n0, no_loops, a, b):
+    m = oracle.num_edges(n, d, n0)
+    b = m if b is None else (m + b if b < 0 else b)
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    got = _gpu(ba, seed, n, d, n0, a, b, v)
+    want = oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b)
+    np.testing.assert_array_equal(got, want)
+    # the rejections happened: the plain graph differs from this one on the same range
+    plain = _gpu(ba, seed, n, d, n0, a, b, v & ~SIMPLE)
+    assert (plain[:, 1] != got[:, 1]).any()
+
+
+@pytest.mark.parametrize("a_off,b_off", [(0, 1), (40, 41), (7, 99), (99, 101), (1, 350)])
+def test_wide_ranges_inside_and_across_nodes(ba, a_off, b_off):
+    # d = 100: ranges that start and end inside nodes, down to a single edge
+    seed, n, d = 48, 3_000, 100
+    base = 100 * 57
+    got = _gpu(ba, seed, n, d, 0, base + a_off, base + b_off, SIMPLE)
+    np.testing.assert_array_equal(got, oracle.edges_range_simple(seed, n, d, 0, False,
+                                                                 base + a_off, base + b_off))
+
+
+@pytest.mark.parametrize("no_loops,n0", [(False, 0), (True, 101)])
+def test_wide_64bit_positions_and_property(ba, no_loops, n0):
+    seed, n, d = 49, 2**26, 100
+    m = oracle.num_edges(n, d, n0)
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    a, b = m - 100_037, m - 13
+    np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b, v),
+                                  oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b))
+    # a 2^24-edge prefix block: every node whose reach covers d has d distinct targets
+    lo = (n0 * (n0 - 1)) // 2 + 200 * d
+    hi = lo + 2**24 // d * d
+    out = torch.from_numpy(_gpu(ba, seed, n, d, n0, lo, hi, v)).cuda()
+    t = out[:, 1].view(-1, d)
+    s_, _ = torch.sort(t, dim=1)
+    assert bool((s_[:, 1:] > s_[:, :-1]).all())
+
+
+@pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", WIDE_CASES[:5])
+def test_wide_degree_count_against_oracle(ba, seed, n, d, n0, no_loops, a, b):
+    m = oracle.num_edges(n, d, n0)
+    b = m if b is None else (m + b if b < 0 else b)
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    limit = min(n, 5_000) + 3
+    want = oracle.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+    counts = torch.full((limit,), 7, dtype=torch.int64, device="cuda")
+    ba.ba_degree_count_variant(seed, n, d, n0, a, b, limit, v, counts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
 
 
 @pytest.mark.parametrize("a_off,b_off", [(0, 1), (3, 5), (5, 37), (1, 64), (15, 33)])
