@@ -54,13 +54,17 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-tune", action="store_true", help="use the library's default shapes")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--table-wave-edges", type=int, default=2**33,
+                    help="edges per wave of the 4096-graph table (16 bytes each on the GPU)")
     ap.add_argument("--cpu-sample-edges", type=int, default=2**28)
     ap.add_argument("--profile", choices=["generate", "degree", "batch", "degree64", "crc",
                                           "simple"],
                     default=None,
                     help="run a small case of one kernel (for ncu captures) and exit")
     ap.add_argument("--profile-edges", type=int, default=2**26)
+    ap.add_argument("--probe", choices=["int", "int64", "write"], default=None,
+                    help="run one roofline probe on a small case (for ncu captures) and exit")
     ap.add_argument("--profile-reps", type=int, default=3)
     return ap.parse_args()
 
@@ -414,28 +418,45 @@ def gpu_arm(args):
     deg_avg = statistics.mean(deg_ms) / 1e3
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     gen_bytes = 16 * m_shard
+    # The roofline's two measured floors, taken live on this GPU after the timed region:
+    # the integer floor (two draws per edge and nothing else) on the position width the
+    # step runs, and the write bandwidth of the generate kernel's 16-byte stores.
+    floors = probe_floors(ba, torch, stream, out, m_shard)
+    r32 = a1 <= 2**31
+    int_floor_ms = floors["int_floor_ms_r32" if r32 else "int_floor_ms_r64"]
+    hbm_floor_ms = gen_bytes / (floors["hbm_write_gbs"] * 1e9) * 1e3
     gen_traffic = recorded_traffic("k_generate_refill")
+    gen_floor_ms = max(int_floor_ms, hbm_floor_ms)
     roof_gen = {"kernel": "k_generate_refill", "bound": "hbm",
                 "achieved": gen_bytes / gen_avg / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": gen_bytes / gen_avg / 1e9 / hbm_peak,
                 "traffic": gen_traffic * m_shard if gen_traffic is not None else None,
                 "peak_source": f"hbm_gbs of {peak_kind} (MEASURED_PEAKS.json copy bandwidth)",
-                "algorithmic_bytes_per_edge": 16, "ms": gen_avg * 1e3}
-    # ALU roofline of the degree count: 1 warp instruction per SMSP per clock at the
-    # maximum SM clock, against the algorithmic instruction count per edge of the 32-bit
-    # position path (hash 24 + stop test 1 per hash, 2.0 hashes per edge, 2 per edge for
-    # the hit test).
+                "algorithmic_bytes_per_edge": 16, "ms": gen_avg * 1e3,
+                "int_floor_ms": int_floor_ms, "hbm_write_gbs": floors["hbm_write_gbs"],
+                "hbm_write_floor_ms": hbm_floor_ms,
+                "binding": "hbm" if hbm_floor_ms >= int_floor_ms else "int",
+                "frac_min_int_hbm": gen_floor_ms / (gen_avg * 1e3)}
+    # The degree count stores nothing: its roofline is the integer floor alone (the same
+    # probe), given here as edges/s.  For context, the SM issue rate from the unit counts
+    # and the maximum clock.
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
-    alu_peak = sms * SMSP_PER_SM * 32 * sm_max * 1e6 / 1e12      # tera thread-instr/s
-    instr_per_edge = 2.0 * 25 + 2
-    deg_achieved = instr_per_edge * m_shard / deg_avg / 1e12
-    deg_traffic = recorded_traffic("k_degree_refill")
-    roof_deg = {"kernel": "k_degree_refill", "bound": "alu", "achieved": deg_achieved,
-                "peak": alu_peak, "unit": "Tinstr/s", "frac": deg_achieved / alu_peak,
+    issue_peak = sms * SMSP_PER_SM * 32 * sm_max * 1e6 / 1e12      # tera thread-instr/s
+    deg_refill = ba.ba_get_tuning(ba.BA_KIND_DEGREE, a1)["refill"]
+    deg_kernel = "k_degree_lane" if deg_refill == 2 else "k_degree_refill"
+    deg_traffic = recorded_traffic(deg_kernel)
+    roof_deg = {"kernel": deg_kernel, "bound": "alu", "achieved": m_shard / deg_avg,
+                "peak": m_shard / (int_floor_ms / 1e3), "unit": "edges/s",
+                "frac": int_floor_ms / (deg_avg * 1e3),
                 "traffic": deg_traffic * m_shard if deg_traffic is not None else None,
-                "peak_source": f"{sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz",
-                "algorithmic_instr_per_edge": instr_per_edge, "ms": deg_avg * 1e3}
+                "peak_source": "measured integer floor: ba_probe_hash (two draws per edge, "
+                               "4 chains per thread, nothing else), "
+                               f"{'32' if r32 else '64'}-bit positions",
+                "ms": deg_avg * 1e3, "int_floor_ms": int_floor_ms,
+                "binding": "int", "frac_min_int_hbm": int_floor_ms / (deg_avg * 1e3),
+                "issue_peak_tinstr_s": issue_peak,
+                "issue_peak_source": f"{sms} SMs x 4 SMSPs x 32 lanes x {sm_max:.0f} MHz"}
     dominant = roof_gen if gen_avg >= deg_avg else roof_deg
 
     result = {
@@ -451,6 +472,7 @@ def gpu_arm(args):
                    "tuning": tuned or "library defaults"},
         "roofline": dominant,
         "roofline_kernels": [roof_gen, roof_deg],
+        "roofline_probes": floors,
         "clocks": clk,
         "gpu_launches": launches,
         "kernels_ms": {"generate": gen_avg * 1e3, "degree": deg_avg * 1e3},
@@ -529,9 +551,11 @@ def extras(args, ba, torch, stream, main):
     counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
     ts = _time_events(lambda: ba.ba_degree_count(g.seed, g.n, g.d, NODE_LIMIT, counts, stream),
                       stream, torch, 2)
+    floor64 = main["roofline_probes"]["int_floor_ms_r64"] / 1e3 * g.m / main["roofline_probes"]["edges"]
     ex["stream_huge_degree"] = {"workload": "n=1e10 d=100 seed=7, 1e12 edges, degree count of "
                                             "nodes < 1e5 (section 3 experiment at 1/1000 scale)",
                                 "edges_per_s": g.m / min(ts), "seconds": min(ts),
+                                "int_floor_s": floor64, "frac_int_floor": floor64 / min(ts),
                                 "degree_sum_first_1e5": int(counts.sum())}
     # the large workload with 32-bit node IDs (8 bytes per edge)
     gl = W.PLAIN_LARGE
@@ -595,9 +619,60 @@ def extras(args, ba, torch, stream, main):
                      "vs_plain_calls_same_graphs": statistics.median(tp) / statistics.median(ts)}
     del out_b
     torch.cuda.empty_cache()
+    ex["batched_table"] = batched_table(args, ba, torch, stream, plain_rate)
+    torch.cuda.empty_cache()
     ex["variants"] = variants(ba, torch, stream, main)
     ex["serving"] = serving(args, ba, torch, plain_rate)
     return ex
+
+
+def batched_table(args, ba, torch, stream, plain_rate):
+    """All 4096 graphs of the batched table (about 7.3e10 edges, 1.17 TB of pairs) in waves
+    of at most --table-wave-edges edges, one persistent launch (a CUDA-graph replay) per
+    wave.  edges/s = all edges / the sum of the waves' CUDA-event times (first replay of a
+    wave after its graph is instantiated).  After each wave, every 16th graph (and the
+    wave's first and last) is compared on the GPU with ba_generate_edges on the same graph;
+    the tests compare the whole table with the oracle."""
+    table = W.batch_table()
+    budget = args.table_wave_edges
+    waves, cur, tot = [], [], 0
+    for gg in table:
+        if cur and tot + gg.m > budget:
+            waves.append(cur)
+            cur, tot = [], 0
+        cur.append(gg)
+        tot += gg.m
+    if cur:
+        waves.append(cur)
+    cap = max(sum(g.m for g in w) for w in waves)
+    out_b = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
+    scratch = torch.empty((max(g.m for g in table), 2), dtype=torch.int64, device="cuda")
+    secs, edges, compared, equal, index = 0.0, 0, 0, 0, 0
+    for w in waves:
+        graphs = [(gg.seed, gg.n, gg.d, gg.n0, 0, gg.m) for gg in w]
+        plan = ba.ba_batch_plan_create(graphs)
+        try:
+            ba.ba_batch_plan_launch(plan, out_b, stream)          # instantiates the CUDA graph
+            ts = _time_events(lambda: ba.ba_batch_plan_launch(plan, out_b, stream), stream, torch, 1)
+        finally:
+            ba.ba_batch_plan_destroy(plan)
+        secs += ts[0]
+        wave_edges = sum(gg.m for gg in w)
+        edges += wave_edges
+        off = 0
+        for k, gg in enumerate(w):
+            if (index + k) % 16 == 0 or k == 0 or k == len(w) - 1:
+                ba.ba_generate_edges(gg.seed, gg.n, gg.d, gg.n0, 0, gg.m, scratch, stream)
+                equal += int(torch.equal(out_b[off:off + gg.m], scratch[:gg.m]))
+                compared += 1
+            off += gg.m
+        index += len(w)
+    del out_b, scratch
+    return {"workload": "the whole 4096-graph table (seed 1000+g, n log-uniform 1e3..1e7, d 1..32, "
+                        f"half clique seeds): {edges} edges, {len(waves)} waves of <= {budget} edges",
+            "graphs": len(table), "waves": len(waves), "edges": edges, "seconds": secs,
+            "edges_per_s": edges / secs, "vs_plain": edges / secs / plain_rate,
+            "graphs_compared_with_plain_calls": compared, "graphs_equal": equal}
 
 
 def variants(ba, torch, stream, main):
@@ -658,7 +733,19 @@ def variants(ba, torch, stream, main):
 
 
 def serving(args, ba, torch, plain_rate):
+    import numpy as np
     trace = W.serving_trace(rate=2000.0, duration=args.serve_seconds)
+    # a seeded 1 % sample of the requests: each result is copied out of the server before
+    # its release and compared on the GPU with the plain entry point on the same range
+    # (the plain entry point is the one the tests check against the oracle)
+    pick = np.random.Generator(np.random.PCG64(11)).choice(
+        len(trace), size=max(1, len(trace) // 100), replace=False)
+    sample = set(int(k) for k in pick)
+    big = max(trace[k].edge_end - trace[k].edge_begin for k in sample)
+    got_buf = torch.empty((big, 2), dtype=torch.int64, device="cuda")
+    want_buf = torch.empty((big, 2), dtype=torch.int64, device="cuda")
+    check_stream = torch.cuda.Stream()
+    sample_exact = 0
     srv = ba.ba_server_create(memory_budget_bytes=96 << 30, chunk_edges=1 << 24, max_active=256)
     lat = []
     edges = 0
@@ -692,6 +779,14 @@ def serving(args, ba, torch, plain_rate):
                 _, l_ns = ba.ba_server_poll(srv, t)
                 lat.append(l_ns / 1e6)
                 edges += length
+                if k in sample:
+                    r = trace[k]
+                    ln = r.edge_end - r.edge_begin
+                    ba.ba_server_copy_result(srv, t, got_buf, check_stream)
+                    ba.ba_generate_edges(r.graph.seed, r.graph.n, r.graph.d, 0, r.edge_begin,
+                                         r.edge_end, want_buf, check_stream)
+                    check_stream.synchronize()
+                    sample_exact += int(torch.equal(got_buf[:ln], want_buf[:ln]))
                 ba.ba_server_release(srv, t)
                 k += 1
         th.join()
@@ -722,10 +817,13 @@ def serving(args, ba, torch, plain_rate):
                              scratch, s)
     torch.cuda.synchronize()
     plain_same = sat_edges / (time.perf_counter() - t0)
-    del scratch
+    del scratch, got_buf, want_buf
     lat.sort()
     return {"workload": f"Poisson 2000 req/s for {args.serve_seconds:g} s ({len(trace)} requests; "
                         "n log-uniform 1e4..1e9, d in {2,4,8,16,32}, 1e4..1e8 edges each)",
+            "sample_checked": len(sample), "sample_exact": sample_exact,
+            "sample_check": "seeded 1 % of the requests, copied out before release and compared "
+                            "on the GPU with ba_generate_edges on the same range",
             "p50_ms": lat[len(lat) // 2] if lat else None,
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
             "edges_per_s_offered_load": edges / wall, "requests": len(lat),
@@ -736,8 +834,55 @@ def serving(args, ba, torch, plain_rate):
             "saturation_vs_plain_same_requests": (sat_edges / sat_dt) / plain_same}
 
 
+def probe_case(args):
+    """One roofline probe on a small case: the two-draw integer floor on 2^26 edges (32-bit
+    or 64-bit positions) or 16-byte streaming stores over 1 GiB, for ncu."""
+    import torch
+
+    from paper_1602_07106_gb300 import build as ba_build
+    ba_build.build()
+    from paper_1602_07106_gb300 import ba
+    stream = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    e = args.profile_edges
+    for _ in range(args.profile_reps):
+        if args.probe == "int":
+            ba.ba_probe_hash(42, 0, e, 4, sink, stream)
+        elif args.probe == "int64":
+            ba.ba_probe_hash(7, 2**40, e, 4, sink, stream)
+        else:
+            buf = torch.empty(2**30, dtype=torch.uint8, device="cuda")
+            ba.ba_probe_write(buf, stream=stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "edges": e, "reps": args.profile_reps}))
+    return 0
+
+
+def probe_floors(ba, torch, stream, buf, edges: int) -> dict:
+    """Measured roofline denominators on this GPU, taken live (CUDA events, median of 3):
+    the integer floor of `edges` edges at two draws each (ba_probe_hash, 4 chains per
+    thread, 32-bit and 64-bit positions) and the write bandwidth of 16-byte streaming
+    stores over `buf` (ba_probe_write)."""
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    res = {}
+    for name, base in (("int_floor_ms_r32", 0), ("int_floor_ms_r64", 2**40)):
+        e = min(edges, 2**31) if base == 0 else edges
+        ts = _time_events(lambda: ba.ba_probe_hash(42, base, e, 4, sink, stream), stream, torch, 3)
+        res[name] = statistics.median(ts) * 1e3 * edges / e
+    nbytes = buf.numel() * buf.element_size()
+    ts = _time_events(lambda: ba.ba_probe_write(buf, nbytes, stream), stream, torch, 3)
+    res["hbm_write_gbs"] = nbytes / statistics.median(ts) / 1e9
+    res["edges"] = edges
+    res["how"] = ("int floor: ba_probe_hash, exactly two draws per edge (section 2's expected "
+                  "chain length) with no scheduling, stop test or store; write: ba_probe_write, "
+                  "16-byte streaming stores over the step's output buffer")
+    return res
+
+
 def main():
     args = parse_args()
+    if args.probe:
+        return probe_case(args)
     if args.profile:
         return profile_case(args)
     if args.impl == "reference":

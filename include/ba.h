@@ -71,6 +71,11 @@ const char *ba_last_error_message(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int ba_version(void);
 
+/* Number of device-memory allocations libba has made in this process since it was loaded:
+ * every stream-ordered allocation from its pool and every cudaMalloc (batch plans, server
+ * arenas and tables).  Lets a caller check that a call allocated nothing. */
+uint64_t ba_device_allocations(void);
+
 /* m = n0(n0-1)/2 + (n-n0) d (section 4), or 0 when (n, d, n0) breaks the argument rules
  * or m > 2^62.  A valid graph can have m = 0 too (n = n0 = 1); a call with an empty range,
  * e.g. ba_generate_edges(..., 0, 0, NULL, ...), tells the two apart by its status. */
@@ -299,8 +304,9 @@ ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
  * (the per-graph constant table, the tile prefix and the tile counter) lives in one static
  * device array of about 114 KB that every GPU loading libba holds until the process exits.
  *  - At most BA_NOALLOC_MAX_GRAPHS graphs per call; a larger G returns BA_ERR_INVALID_ARG.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *  - The first call on a device (and the first after that device's context was reset)
+ *    looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ *    make that first call before any stream capture.
  *  - The descriptor table is copied from host memory on `stream`; a copy from pageable
  *    memory waits for the work already on `stream`.  The tile counter is cleared on every
  *    call; the tables are rewritten in full.

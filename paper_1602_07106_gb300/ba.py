@@ -97,6 +97,7 @@ _sig("ba_generate_batch", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp
      ctypes.POINTER(ba_tuning), _vp)
 _sig("ba_generate_batch_noalloc", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp, _vp,
      _vp)
+_sig("ba_device_allocations", _u64)
 _sig("ba_probe_hash", ctypes.c_int, _u64, _u64, _u64, _i32, _vp, _vp)
 _sig("ba_probe_write", ctypes.c_int, _vp, _u64, _vp)
 _sig("ba_server_create", ctypes.c_int, ctypes.POINTER(ba_server_config), ctypes.POINTER(_vp))
@@ -263,16 +264,18 @@ def _descs(graphs) -> tuple[ctypes.Array, int]:
     return arr, len(graphs)
 
 
-def _offsets_arg(offsets):
+def _offsets_arg(offsets, G: int):
     if offsets is None:
         return None, None
+    if len(offsets) != G + 1:
+        raise ValueError(f"offsets needs G + 1 = {G + 1} entries, got {len(offsets)}")
     arr = (ctypes.c_int64 * len(offsets))(*[int(x) for x in offsets])
     return arr, ctypes.addressof(arr)
 
 
 def ba_batch_plan_create(graphs, offsets=None, tune=None) -> int:
     arr, G = _descs(graphs)
-    keep, off = _offsets_arg(offsets)
+    keep, off = _offsets_arg(offsets, G)
     t = _tuning(tune)
     plan = _vp()
     _check(_lib.ba_batch_plan_create(arr, G, off, ctypes.byref(t) if t is not None else None,
@@ -300,7 +303,7 @@ def ba_batch_plan_destroy(plan: int) -> None:
 
 def ba_generate_batch(graphs, out, offsets=None, tune=None, stream=None) -> None:
     arr, G = _descs(graphs)
-    keep, off = _offsets_arg(offsets)
+    keep, off = _offsets_arg(offsets, G)
     t = _tuning(tune)
     _check(_lib.ba_generate_batch(arr, G, off, _ptr(out), ctypes.byref(t) if t is not None else None,
                                   _stream(stream)), "ba_generate_batch")
@@ -314,9 +317,14 @@ def ba_generate_batch_noalloc(graphs, out, offsets=None, stream=None) -> None:
     static device table (at most BA_NOALLOC_MAX_GRAPHS graphs); calls that overlap on the
     GPU share that table and must be serialised by the caller."""
     arr, G = _descs(graphs)
-    keep, off = _offsets_arg(offsets)
+    keep, off = _offsets_arg(offsets, G)
     _check(_lib.ba_generate_batch_noalloc(arr, G, off, _ptr(out), _stream(stream)),
            "ba_generate_batch_noalloc")
+
+
+def ba_device_allocations() -> int:
+    """Device allocations libba has made in this process so far."""
+    return int(_lib.ba_device_allocations())
 
 
 def ba_probe_hash(seed, base, edges, chains, sink, stream=None) -> None:

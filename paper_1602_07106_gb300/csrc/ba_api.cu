@@ -1,5 +1,6 @@
 // ba_api.cu -- the C ABI of libba (include/ba.h): argument checks, per-call scratch and
 // the launches of the plain entry points.
+#include <atomic>
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -71,6 +72,7 @@ void set_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
 ba_status pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
   *ptr = nullptr;
+  count_device_allocation();
   cudaMemPool_t pool = nullptr;
   cudaError_t e = library_pool(&pool);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
@@ -83,6 +85,12 @@ ba_status pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
   }
   return BA_OK;
 }
+
+namespace {
+std::atomic<unsigned long long> g_device_allocations{0};
+}
+
+void count_device_allocation() { g_device_allocations.fetch_add(1, std::memory_order_relaxed); }
 
 int adapt_tile(uint64_t total_edges, const Shape &s) {
   const uint64_t warps = static_cast<uint64_t>(sm_count()) * std::max(s.ctas_per_sm, 1) *
@@ -187,6 +195,8 @@ const char *ba_status_string(int status) {
 const char *ba_last_error_message(void) { return g_last_error.c_str(); }
 
 int ba_version(void) { return 10000; }
+
+uint64_t ba_device_allocations(void) { return g_device_allocations.load(std::memory_order_relaxed); }
 
 uint64_t ba_num_edges(uint64_t n, uint32_t d, uint64_t n0) {
   uint64_t m = 0;

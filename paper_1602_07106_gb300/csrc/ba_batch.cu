@@ -119,9 +119,9 @@ ba_status ba_batch_plan_create(const ba_graph_desc *descs, int32_t G, const int6
     return st;
   }
   cudaError_t e;
-  if ((e = cudaMalloc(&p->d_graphs, std::max<size_t>(1, p->graphs.size()) * sizeof(GraphDev))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_prefix, p->prefix.size() * sizeof(uint64_t))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_counter, 256)) != cudaSuccess ||
+  if ((count_device_allocation(), e = cudaMalloc(&p->d_graphs, std::max<size_t>(1, p->graphs.size()) * sizeof(GraphDev))) != cudaSuccess ||
+      (count_device_allocation(), e = cudaMalloc(&p->d_prefix, p->prefix.size() * sizeof(uint64_t))) != cudaSuccess ||
+      (count_device_allocation(), e = cudaMalloc(&p->d_counter, 256)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_graphs, p->graphs.data(), p->graphs.size() * sizeof(GraphDev),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_prefix, p->prefix.data(), p->prefix.size() * sizeof(uint64_t),

@@ -48,6 +48,8 @@ int sm_count();
 // Stream-ordered scratch from libba's own pool on the current device (kept mapped up to
 // 64 MB between calls); release with cudaFreeAsync on the same stream.
 ba_status pool_alloc(void **ptr, size_t bytes, cudaStream_t s);
+// Counts one device allocation (pool_alloc does; so does every cudaMalloc of the library).
+void count_device_allocation();
 // Tile size for a batched launch of `total_edges` edges with shape s: the shape's tile,
 // halved (down to 256) until every warp of a full grid has about four tiles, as plain
 // calls do, so that small batches and light serving ticks still spread over the GPU.

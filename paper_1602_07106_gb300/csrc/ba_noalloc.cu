@@ -10,8 +10,9 @@
 // fixed size, reserved when the library's module is loaded on a GPU and held until exit.
 //
 // Host code never hands the array's name to a kernel (in host code the name is only a
-// host-side stand-in): the array's device address is looked up with cudaGetSymbolAddress
-// once per device, with that device current, on the first call made on it.
+// host-side stand-in): the array's device address is looked up with cudaGetSymbolAddress,
+// with the device current, on the first call made on it (and again after its context was
+// reset).
 #include <mutex>
 
 #include "ba_internal.h"
@@ -32,8 +33,41 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// ID of the current CUDA context (unique for the process's lifetime, so a context created
+// again after a reset gets a new one), through the driver's entry points; false when no
+// context is current or the driver does not offer the calls.
+bool current_context_id(unsigned long long *id) {
+  using GetCurrent = int (*)(void **);
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f);
+      get_id = reinterpret_cast<GetId>(g);
+    }
+    cudaGetLastError();
+  }
+  if (get_current == nullptr || get_id == nullptr) return false;
+  void *ctx = nullptr;
+  if (get_current(&ctx) != 0 || ctx == nullptr) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of g_noalloc_scratch on the current device.  Looked up (with that device
+// current) on the first call made on the device, and again whenever the current context
+// is not the one the cached address came from (after a reset the module is loaded anew and
+// the array may have moved).  Without the driver's context IDs it is looked up every call.
 ba_status scratch_address(NoAllocScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -43,11 +77,14 @@ ba_status scratch_address(NoAllocScratch **out) {
     return BA_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (g_scratch_addr[dev] == nullptr) {
+  unsigned long long id = 0;
+  const bool known = current_context_id(&id);
+  if (g_scratch_addr[dev] == nullptr || !known || id != g_scratch_ctx[dev]) {
     void *ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e, "cudaGetSymbolAddress");
     g_scratch_addr[dev] = ptr;
+    g_scratch_ctx[dev] = current_context_id(&id) ? id : 0;  // the lookup made one current
   }
   *out = static_cast<NoAllocScratch *>(g_scratch_addr[dev]);
   return BA_OK;
@@ -102,7 +139,9 @@ extern "C" ba_status ba_generate_batch_noalloc(const ba_graph_desc *descs, int32
   ba_status st = scratch_address(&scratch);
   if (st != BA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Shape shape = shape_for(BA_KIND_BATCH, r32);
+  // the same launch shape as ba_generate_batch: the tuned tile, shrunk for small batches
+  Shape shape = shape_for(BA_KIND_BATCH, r32);
+  shape.tile = adapt_tile(total_edges, shape);
   const uint64_t T = static_cast<uint64_t>(shape.tile);
 
   // Pass 2: build the tables in small stack blocks and copy each into the scratch.  A copy

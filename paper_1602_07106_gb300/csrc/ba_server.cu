@@ -311,7 +311,7 @@ ba_status ba_server_create(const ba_server_config *cfg, ba_server **server) {
   }
   s->arena_edges = s->cfg.memory_budget_bytes / 16;
   ba_status st = BA_OK;
-  if ((e = cudaMalloc(&s->arena_base, std::max<uint64_t>(s->arena_edges, 1) * 16)) != cudaSuccess) {
+  if ((count_device_allocation(), e = cudaMalloc(&s->arena_base, std::max<uint64_t>(s->arena_edges, 1) * 16)) != cudaSuccess) {
     st = e == cudaErrorMemoryAllocation ? BA_ERR_NOMEM : cuda_fail(e, "cudaMalloc(arena)");
   } else if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
     st = cuda_fail(e, "cudaStreamCreateWithFlags");
@@ -324,9 +324,9 @@ ba_status ba_server_create(const ba_server_config *cfg, ba_server **server) {
     if (st != BA_OK) break;
     if ((e = cudaMallocHost(&slot.host_tab, 2 * cap * sizeof(GraphDev))) != cudaSuccess ||
         (e = cudaMallocHost(&slot.host_prefix, 2 * (cap + 1) * sizeof(uint64_t))) != cudaSuccess ||
-        (e = cudaMalloc(&slot.dev_tab, 2 * cap * sizeof(GraphDev))) != cudaSuccess ||
-        (e = cudaMalloc(&slot.dev_prefix, 2 * (cap + 1) * sizeof(uint64_t))) != cudaSuccess ||
-        (e = cudaMalloc(&slot.dev_counter, 512)) != cudaSuccess)
+        (count_device_allocation(), e = cudaMalloc(&slot.dev_tab, 2 * cap * sizeof(GraphDev))) != cudaSuccess ||
+        (count_device_allocation(), e = cudaMalloc(&slot.dev_prefix, 2 * (cap + 1) * sizeof(uint64_t))) != cudaSuccess ||
+        (count_device_allocation(), e = cudaMalloc(&slot.dev_counter, 512)) != cudaSuccess)
       st = e == cudaErrorMemoryAllocation ? BA_ERR_NOMEM : cuda_fail(e, "server tick tables");
   }
   if (st != BA_OK) {

@@ -133,6 +133,16 @@ def test_tuning_overrides_validate_and_round_trip(tmp_path):
         ba.ba_tune_load(str(tmp_path / "missing.json"))
 
 
+def test_offsets_need_one_entry_per_graph_plus_one():
+    graphs = [(1, 10, 1, 0, 0, 5), (2, 10, 1, 0, 0, 5)]
+    for fn in (ba.ba_generate_batch, ba.ba_generate_batch_noalloc):
+        with pytest.raises(ValueError):
+            fn(graphs, out=0x1000, offsets=[0, 5], stream=0)      # G + 1 = 3 needed
+    with pytest.raises(ValueError):
+        ba.ba_batch_plan_create(graphs, offsets=[0, 5, 10, 15])
+    assert ba.ba_device_allocations() >= 0
+
+
 def test_lane_chunk_shapes_are_degree_only():
     # refill 2 (lane chunks) exists for the degree count only; its chunk is a power of two
     for kind in (ba.BA_KIND_GENERATE, ba.BA_KIND_BATCH):

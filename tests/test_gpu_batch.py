@@ -110,3 +110,46 @@ def test_batch_workload_first_wave_exact(ba):
         _check_against_oracle(host, graphs, offsets)
     finally:
         ba.ba_batch_plan_destroy(plan)
+
+
+def test_batch_workload_whole_table_every_graph_exact(ba):
+    # All 4096 graphs of the batched workload (7.6e10 edges, 1.2 TB of pairs) in waves of at
+    # most 2^32 edges, one persistent launch per wave; every graph of every wave is checked
+    # against the oracle: in full up to 2e6 edges, else on its first, middle and last 10^5.
+    import multiprocessing as mp
+    table = W.batch_table()
+    budget = 2**32
+    waves, cur, tot = [], [], 0
+    for g in table:
+        if cur and tot + g.m > budget:
+            waves.append(cur)
+            cur, tot = [], 0
+        cur.append(g)
+        tot += g.m
+    waves.append(cur)
+    assert sum(len(w) for w in waves) == 4096
+    out = torch.empty((max(sum(g.m for g in w) for w in waves), 2), dtype=torch.int64,
+                      device="cuda")
+    checked = 0
+    oracle.build()
+    with mp.get_context("spawn").Pool(opar.default_workers()) as pool:
+        for w in waves:
+            graphs = [(g.seed, g.n, g.d, g.n0, 0, g.m) for g in w]
+            plan = ba.ba_batch_plan_create(graphs)
+            try:
+                offsets = ba.ba_batch_plan_offsets(plan, len(graphs))
+                ba.ba_batch_plan_launch(plan, out)
+                torch.cuda.synchronize()
+            finally:
+                ba.ba_batch_plan_destroy(plan)
+            jobs, slices = [], []
+            for k, (seed, n, d, n0, a, b) in enumerate(graphs):
+                spans = [(0, b - a)] if b - a <= 2_000_000 else \
+                    [(0, 100_000), ((b - a) // 2, (b - a) // 2 + 100_000), (b - a - 100_000, b - a)]
+                for lo, hi in spans:
+                    jobs.append((seed, n, d, n0, a + lo, a + hi))
+                    slices.append((offsets[k] + lo, offsets[k] + hi))
+            for (x, y), want in zip(slices, pool.imap(opar._edges_piece, jobs, chunksize=8)):
+                np.testing.assert_array_equal(out[x:y].cpu().numpy(), want)
+            checked += len(graphs)
+    assert checked == 4096

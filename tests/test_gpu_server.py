@@ -128,3 +128,52 @@ def test_autotuner_picks_a_valid_shape_and_output_is_unchanged(ba):
     bshape = ba.ba_tune(ba.BA_KIND_BATCH, 3, n, d, 0, 0, m, scratch)
     assert bshape["block"] % 32 == 0
     assert torch.equal(_plain(ba, 3, n, d, 0, 0, m), before)
+
+
+def test_poisson_trace_sampled_one_percent_exact_against_oracle(ba):
+    # The serving workload's shape (Poisson 2000 req/s, n log-uniform 1e4..1e9, d in
+    # {2,..,32}, 1e4..1e8 edges) for 3 s of arrivals in real time; a seeded 1 % of the
+    # requests is copied out of the server before release and checked against the oracle
+    # (in full up to 2e6 edges, else on its first, middle and last 10^5 edges).
+    import threading
+    import time
+    from oracle import parallel as opar
+    trace = W.serving_trace(rate=2000.0, duration=3.0, trace_seed=17)
+    pick = set(int(k) for k in np.random.Generator(np.random.PCG64(19)).choice(
+        len(trace), size=len(trace) // 100, replace=False))
+    srv = ba.ba_server_create(memory_budget_bytes=64 << 30, chunk_edges=1 << 24, max_active=256)
+    tickets = [None] * len(trace)
+    kept = {}
+    try:
+        def submit():
+            t0 = time.perf_counter()
+            for k, r in enumerate(trace):
+                delay = r.t_arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = ba.ba_server_submit(srv, r.graph.seed, r.graph.n, r.graph.d, 0,
+                                                 r.edge_begin, r.edge_end)
+        th = threading.Thread(target=submit)
+        th.start()
+        for k, r in enumerate(trace):
+            while tickets[k] is None:
+                time.sleep(0.0005)
+            ba.ba_server_wait(srv, tickets[k], 600_000)
+            if k in pick:
+                res = ba.server_result_tensor(srv, tickets[k])
+                ln = r.edge_end - r.edge_begin
+                spans = [(0, ln)] if ln <= 2_000_000 else \
+                    [(0, 100_000), (ln // 2, ln // 2 + 100_000), (ln - 100_000, ln)]
+                kept[k] = [(lo, hi, res[lo:hi].cpu().numpy()) for lo, hi in spans]
+            ba.ba_server_release(srv, tickets[k])
+        th.join()
+        assert ba.ba_server_stats_get(srv)["bytes_in_use"] == 0
+    finally:
+        ba.ba_server_destroy(srv)
+    assert len(kept) == len(pick) >= 50
+    for k, spans in kept.items():
+        r = trace[k]
+        for lo, hi, got in spans:
+            np.testing.assert_array_equal(
+                got, opar.edges_range(r.graph.seed, r.graph.n, r.graph.d, 0,
+                                      r.edge_begin + lo, r.edge_begin + hi))

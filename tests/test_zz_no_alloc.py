@@ -28,8 +28,12 @@ def test_noalloc_batch_matches_allocating_batch_on_two_calls_in_a_row(ba):
     second, total2 = _batch(202, 1024)       # the largest batch the static table holds
     out1 = torch.full((total1, 2), -1, dtype=torch.int64, device="cuda")
     out2 = torch.full((total2, 2), -1, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    allocs = ba.ba_device_allocations()
     ba.ba_generate_batch_noalloc(first, out1)
     ba.ba_generate_batch_noalloc(second, out2)
+    torch.cuda.synchronize()
+    assert ba.ba_device_allocations() == allocs      # the two calls allocated nothing
     want1 = torch.empty_like(out1)
     want2 = torch.empty_like(out2)
     ba.ba_generate_batch(first, want1)
@@ -40,9 +44,15 @@ def test_noalloc_batch_matches_allocating_batch_on_two_calls_in_a_row(ba):
     # the scratch keeps the previous call's contents: a smaller batch after a larger one
     # must not see stale graphs or a stale tile counter
     out3 = torch.full((total1, 2), -1, dtype=torch.int64, device="cuda")
+    allocs = ba.ba_device_allocations()
     ba.ba_generate_batch_noalloc(first, out3)
     torch.cuda.synchronize()
+    assert ba.ba_device_allocations() == allocs
     assert torch.equal(out3, want1)
+    # the allocating entry point is counted, so the counter does see allocations
+    ba.ba_generate_batch(first, want1)
+    torch.cuda.synchronize()
+    assert ba.ba_device_allocations() > allocs
 
 
 def test_noalloc_batch_with_offsets_and_rejections(ba):
