@@ -444,7 +444,7 @@ def gpu_arm(args):
     sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
     issue_peak = sms * SMSP_PER_SM * 32 * sm_max * 1e6 / 1e12      # tera thread-instr/s
     deg_refill = ba.ba_get_tuning(ba.BA_KIND_DEGREE, a1)["refill"]
-    deg_kernel = "k_degree_lane" if deg_refill == 2 else "k_degree_refill"
+    deg_kernel = "k_degree_refill" if deg_refill == 1 else "k_degree_simple"
     deg_traffic = recorded_traffic(deg_kernel)
     roof_deg = {"kernel": deg_kernel, "bound": "alu", "achieved": m_shard / deg_avg,
                 "peak": m_shard / (int_floor_ms / 1e3), "unit": "edges/s",

@@ -190,17 +190,13 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
  *  tile         edges per warp tile (power of two, 64..2^20); plain calls halve it,
  *               down to 256, until every warp of the grid gets several tiles
  *  refill       0 = one thread per edge, no refill (the simple kernel);
- *               1 = warp refill every hash step (ballot/popc compaction);
- *               2 = lane chunks (degree count only): each lane walks its own run of
- *                   consecutive edge IDs, no per-step compaction
+ *               1 = warp refill every hash step (ballot/popc compaction)
  *  hist_bins    degree kernel: shared-memory histogram bins per CTA
  *  hist_agg     degree kernel: 1 = one shared-memory atomic per distinct node per warp
  *               (__match_any_sync aggregation), 0 = one atomic per hitting lane
  *  chains       refill kernels: hash chains each lane keeps in flight (1 or 2); a
  *               second independent chain hides the latency of the hash's dependent
- *               multiplies
- *  lane_chunk   refill = 2 degree count: edges per lane chunk (power of two 32..1024,
- *               0 = default) */
+ *               multiplies */
 typedef struct ba_tuning {
     int32_t block;
     int32_t ctas_per_sm;
@@ -209,7 +205,7 @@ typedef struct ba_tuning {
     int32_t hist_bins;
     int32_t hist_agg;
     int32_t chains;
-    int32_t lane_chunk;
+    int32_t reserved;
 } ba_tuning;
 
 /* Kernel families the tuner keys on. */

@@ -36,12 +36,12 @@ _vp = ctypes.c_void_p
 class ba_tuning(ctypes.Structure):
     _fields_ = [("block", _i32), ("ctas_per_sm", _i32), ("tile", _i32), ("refill", _i32),
                 ("hist_bins", _i32), ("hist_agg", _i32), ("chains", _i32),
-                ("lane_chunk", _i32)]
+                ("reserved", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k)
                 for k in ("block", "ctas_per_sm", "tile", "refill", "hist_bins", "hist_agg",
-                          "chains", "lane_chunk")}
+                          "chains")}
 
 
 class ba_graph_desc(ctypes.Structure):

@@ -19,8 +19,11 @@
 
 namespace ba {
 
-// Ptx: the 32-bit path uses hash_r32_pre_ptx (same values; faster in the degree kernel).
-template <bool Ptx>
+// Ptx32 / Ptx64: the hash written in PTX on 32-bit / 64-bit positions (hash_r32_pre_ptx,
+// hash_r64_pre_ptx; same values as the C forms).  Measured per kernel: the PTX forms are
+// faster in the degree count on both widths and in generate on 64-bit positions; on
+// 32-bit positions the generate kernel is faster with the compiler's lowering.
+template <bool Ptx32, bool Ptx64>
 struct DrawPlainT {
   static constexpr bool kPlain = true;
   static constexpr bool kTables = false;
@@ -32,12 +35,14 @@ struct DrawPlainT {
   __device__ __forceinline__ void bind(const GraphDev &g) { spre = g.seed_pre; }
   template <class RT>
   __device__ __forceinline__ RT operator()(RT r) const {
-    if constexpr (Ptx && sizeof(RT) == 4) return hash_r32_pre_ptx(spre, r);
+    if constexpr (sizeof(RT) == 4 && Ptx32) return hash_r32_pre_ptx(spre, r);
+    else if constexpr (sizeof(RT) == 8 && Ptx64) return hash_r64_pre_ptx(spre, r);
     else return hash_pre<RT>(spre, r);
   }
 };
-using DrawPlain = DrawPlainT<false>;
-using DrawPlainPtx = DrawPlainT<true>;
+using DrawPlain = DrawPlainT<false, false>;    // the C form everywhere
+using DrawPlainGen = DrawPlainT<false, true>;  // generate and batched kernels
+using DrawPlainPtx = DrawPlainT<true, true>;   // degree count
 
 // CRC-32C in bit-reflected form (polynomial 0x1EDC6F41 reversed).
 constexpr uint32_t kCrc32cReflected = 0x82F63B78u;

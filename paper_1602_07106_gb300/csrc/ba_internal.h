@@ -17,7 +17,7 @@ struct SchedParams {
   uint32_t tile_shift;
   uint32_t total_warps;          // warps in the grid (first tile of warp w is w)
   uint32_t hist_agg;             // degree kernel: warp-aggregate histogram increments
-  uint32_t lane_chunk;           // lane-chunk kernels: edges per lane chunk
+  uint32_t pad;
 };
 
 // Graph table of a batched launch (device pointers).
@@ -35,7 +35,6 @@ struct Shape {
   int hist_bins = 0;
   int hist_agg = 0;
   int chains = 1;  // hash chains per lane in the generate / batched refill kernels
-  int lane_chunk = 0;  // refill = 2 degree kernel: edges per lane chunk (0 = default)
 };
 
 // ---- host helpers (ba_api.cu)

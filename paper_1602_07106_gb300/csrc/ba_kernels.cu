@@ -588,139 +588,11 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   }
 }
 
-// --------------------------------------------------------- lane-chunk degree kernel --
-//
-// Lane chunks (refill = 2) for the degree count: each lane walks a chunk of sp.lane_chunk
-// consecutive edge IDs of its own, one draw per step, so a stopped chain needs no
-// ballot/popc compaction -- the lane just moves on to its next edge.  A chain that stops
-// below hit_pos is counted at once by its lane (a branch that a warp takes in about a
-// third of its steps on the large workload).  After every step one ballot finds the lanes
-// whose chunk is complete and hands them the warp's next chunks (edge order within the
-// warp's tile, tiles from the global counter).  Measured against k_degree_refill: faster
-// on 64-bit positions (the longer hash leaves the per-step compaction a larger share),
-// slower on 32-bit ones; the tuner picks per position width.
-template <class RT, bool HasSeed, class Draw = DrawPlain, int K = 1>
-__global__ void __launch_bounds__(1024, 1)
-k_degree_lane(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64_t node_limit,
-              uint32_t hot, uint64_t *__restrict__ counts) {
-  extern __shared__ __align__(16) unsigned long long bins[];
-  for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) bins[b] = 0;
-  __syncthreads();
-  Draw draw;  // tables (if any) after the bins
-  draw.setup(g, reinterpret_cast<uint32_t *>(bins + hot), sizeof(RT) == 4);
-  draw.bind(g);
-  const int lane = threadIdx.x & 31;
-  const int warps = blockDim.x >> 5;
-  const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + (threadIdx.x >> 5);
-  const uint32_t shift = sp.tile_shift;
-  const uint64_t T = 1ull << shift;
-  const uint32_t chunk = sp.lane_chunk;
-  const RT two_m0 = seed_limit<RT>(g.two_m0);
-  // As a 32-bit position, hit_pos >= 2^32 saturates (every stopped position is below it).
-  const RT hp = (sizeof(RT) == 4 && hit_pos > 0xffffffffull) ? static_cast<RT>(0xffffffffu)
-                                                             : static_cast<RT>(hit_pos);
-  bool first = true;
-  uint64_t tbase = 0;
-  uint32_t tlen = 0, toff = 0;
-  bool have = true;
-
-  // Chain c: current position r[c], first position 2i+1 of its current edge in rn[c], and
-  // 2e+1 for the edge e just past its chunk in rend[c] (modulo 2^32 on the 32-bit path,
-  // where the two wrap alike).
-  RT r[K], rn[K], rend[K];
-  bool idle[K];
-#pragma unroll
-  for (int c = 0; c < K; ++c) {
-    r[c] = rn[c] = rend[c] = 1;
-    idle[c] = false;
-  }
-
-  auto turn_over = [&](int c) {  // warp-uniform
-    uint32_t dm = __ballot_sync(kFull, !idle[c] && rn[c] == rend[c]);
-    while (dm) {
-      const int L = __ffs(dm) - 1;
-      dm &= dm - 1;
-      if (toff >= tlen && have) {
-        const uint64_t t = next_tile(sp, first, gwarp);
-        if (t < sp.num_tiles) {
-          tbase = g.begin + (t << shift);
-          tlen = static_cast<uint32_t>(min(T, g.end - tbase));
-          toff = 0;
-        } else {
-          have = false;
-        }
-      }
-      const uint32_t nlen = have ? min(chunk, tlen - toff) : 0u;
-      const uint64_t nb = tbase + toff;
-      toff += chunk;
-      if (lane == L) {
-        rn[c] = r[c] = static_cast<RT>(2 * nb + 1);
-        rend[c] = static_cast<RT>(2 * (nb + nlen) + 1);
-        idle[c] = nlen == 0;
-      }
-    }
-  };
-
-  auto step = [&](auto live_tag, auto seed_tag) {
-    constexpr bool Live = decltype(live_tag)::value;
-    constexpr bool Seed = decltype(seed_tag)::value;
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-      if (Live && idle[c]) continue;
-      r[c] = draw(r[c]);
-      if (chain_stops<RT, Seed>(r[c], two_m0)) {
-        if (r[c] < hp) {
-          const uint64_t v = target_of<RT, HasSeed>(r[c], g);
-          if (v < node_limit) histogram_add_lane(v, bins, hot, counts);
-        }
-        rn[c] += 2;
-        r[c] = rn[c];
-      }
-    }
-  };
-
-  auto fast = [&](auto seed_tag) {
-    for (;;) {
-      step(std::false_type{}, seed_tag);
-      bool done = false;
-#pragma unroll
-      for (int c = 0; c < K; ++c) done |= rn[c] == rend[c];
-      if (__any_sync(kFull, done)) {
-#pragma unroll
-        for (int c = 0; c < K; ++c) turn_over(c);
-        if (!have) return;
-      }
-    }
-  };
-
-#pragma unroll
-  for (int c = 0; c < K; ++c) turn_over(c);  // the first chunks
-  if (have) {
-    if (HasSeed && two_m0 != 0) fast(std::true_type{});
-    else fast(std::false_type{});
-  }
-  for (;;) {  // the tail: finish the chunks in flight
-    bool live = false;
-#pragma unroll
-    for (int c = 0; c < K; ++c) live |= !idle[c];
-    if (!__any_sync(kFull, live)) break;
-    step(std::true_type{}, std::integral_constant<bool, HasSeed>{});
-#pragma unroll
-    for (int c = 0; c < K; ++c) turn_over(c);
-  }
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
-    const unsigned long long c = bins[b];
-    if (c) atomicAdd(reinterpret_cast<unsigned long long *>(counts + b), static_cast<unsigned long long>(c));
-  }
-}
-
 // ------------------------------------------------------------------------ launchers --
 
 int floor_log2(uint32_t x) { return 31 - __builtin_clz(x); }
 
 constexpr size_t kMaxSmemPerCta = 227 * 1024;  // sm_100-class opt-in limit per CTA
-constexpr int kDefaultDegreeChunk = 128;        // edges per lane chunk of k_degree_lane
 
 template <class K>
 ba_status set_smem(K kernel, size_t smem) {
@@ -756,50 +628,7 @@ ba_status check_launch(const char *what) {
   return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
 }
 
-// Scheduler parameters of a persistent launch over `len` edges: tiles of the shape's size,
-// halved (down to 256) until every warp of the full grid has about four, so that short
-// ranges still spread over the whole GPU; the grid is cut to the warps that have a tile.
-SchedParams sched_for(uint64_t len, const Shape &s, int warps, int *grid,
-                      unsigned long long *counter) {
-  uint32_t shift = static_cast<uint32_t>(floor_log2(static_cast<uint32_t>(s.tile)));
-  const uint64_t all_warps = static_cast<uint64_t>(*grid) * warps;
-  while (shift > 8 && (len >> shift) < 4 * all_warps) --shift;
-  SchedParams sp{};
-  sp.num_tiles = (len + (1ull << shift) - 1) >> shift;
-  sp.counter = counter;
-  sp.tile_shift = shift;
-  sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
-  *grid = static_cast<int>(std::min<uint64_t>(*grid, (sp.num_tiles + warps - 1) / warps));
-  sp.total_warps = static_cast<uint32_t>(*grid) * warps;
-  return sp;
-}
-
-template <class RT, bool HasSeed, class Draw>
-ba_status degree_lane_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uint64_t *counts,
-                        const Shape &s, unsigned long long *counter, cudaStream_t stream) {
-  const uint64_t len = g.end - g.begin;
-  const int block = s.block;
-  const int warps = block / 32;
-  const int K = s.chains == 2 ? 2 : 1;
-  const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
-  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
-                      (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
-  auto kernel = K == 2 ? k_degree_lane<RT, HasSeed, Draw, 2> : k_degree_lane<RT, HasSeed, Draw, 1>;
-  ba_status st = set_smem(kernel, smem);
-  if (st != BA_OK) return st;
-  int grid = 0;
-  st = persistent_grid(kernel, block, smem, s.ctas_per_sm, ~0ull, &grid);
-  if (st != BA_OK) return st;
-  SchedParams sp = sched_for(len, s, warps, &grid, counter);
-  sp.lane_chunk = static_cast<uint32_t>(
-      std::min<int>(s.lane_chunk > 0 ? s.lane_chunk : kDefaultDegreeChunk, 1 << sp.tile_shift));
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  kernel<<<grid, block, smem, stream>>>(g, sp, hit_pos, node_limit, hot, counts);
-  return check_launch("k_degree_lane");
-}
-
-template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlain>
+template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlainGen>
 ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
                      cudaStream_t stream) {
   const uint64_t len = g.end - g.begin;
@@ -860,10 +689,6 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
     }
   }
   const int warps = block / 32;
-  if constexpr (Draw::kPlain) {  // lane chunks: the plain draw only (variants use refill)
-    if (s.refill == 2)
-      return degree_lane_t<RT, HasSeed, Draw>(g, hit_pos, node_limit, counts, s, counter, stream);
-  }
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
                       static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit rings
@@ -899,8 +724,8 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
                       static_cast<size_t>(warps) * sizeof(GraphDev);
-  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, true, false, DrawPlain, 2>
-                              : k_generate_refill<RT, HasSeed, true, false, DrawPlain, 1>;
+  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, true, false, DrawPlainGen, 2>
+                              : k_generate_refill<RT, HasSeed, true, false, DrawPlainGen, 1>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   SchedParams sp{};

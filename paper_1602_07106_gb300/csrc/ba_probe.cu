@@ -6,8 +6,9 @@
 //                  draws h(r) (the expected chain length, section 2's work bound), the
 //                  second keyed by the first result made odd.  C independent chains per
 //                  thread keep the multiplies' latency hidden, so the rate is that of the
-//                  integer pipes alone.  Positions start at 2*base+1: base = 0 takes the
-//                  32-bit-position hash, base >= 2^31 the 64-bit one.
+//                  integer pipes alone.  The draw is the PTX form the kernels use.
+//                  Positions start at 2*base+1: base = 0 takes the 32-bit-position
+//                  hash, base >= 2^31 the 64-bit one.
 //   k_probe_write  16-byte streaming stores over a buffer, nothing read: the write side
 //                  of the generate kernel's roofline (16 bytes per edge).
 #include <algorithm>
@@ -18,6 +19,14 @@ namespace ba {
 namespace {
 
 constexpr uint32_t kFullMask = 0xffffffffu;
+
+// The fastest form of h(r) the kernels use (the PTX one).
+__device__ __forceinline__ uint32_t hash_ptx(uint64_t seed_pre, uint32_t r) {
+  return hash_r32_pre_ptx(seed_pre, r);
+}
+__device__ __forceinline__ uint64_t hash_ptx(uint64_t seed_pre, uint64_t r) {
+  return hash_r64_pre_ptx(seed_pre, r);
+}
 
 template <class RT, int C>
 __global__ void __launch_bounds__(256)
@@ -30,9 +39,9 @@ k_probe_hash(uint64_t seed_pre, uint64_t base, uint64_t edges, unsigned long lon
 #pragma unroll
     for (int c = 0; c < C; ++c) r[c] = static_cast<RT>(2 * (base + e0 + c) + 1);
 #pragma unroll
-    for (int c = 0; c < C; ++c) r[c] = hash_pre<RT>(seed_pre, r[c]);
+    for (int c = 0; c < C; ++c) r[c] = hash_ptx(seed_pre, r[c]);
 #pragma unroll
-    for (int c = 0; c < C; ++c) r[c] = hash_pre<RT>(seed_pre, r[c] | 1);
+    for (int c = 0; c < C; ++c) r[c] = hash_ptx(seed_pre, r[c] | 1);
 #pragma unroll
     for (int c = 0; c < C; ++c)
       if (e0 + c < edges) acc ^= static_cast<uint64_t>(r[c]);

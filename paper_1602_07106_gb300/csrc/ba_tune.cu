@@ -56,7 +56,6 @@ Shape from_public(const ba_tuning &t, int kind) {
   if (t.hist_bins > 0) s.hist_bins = t.hist_bins;
   s.hist_agg = t.hist_agg;
   if (t.chains > 0) s.chains = t.chains;
-  if (t.lane_chunk > 0) s.lane_chunk = t.lane_chunk;
   return s;
 }
 
@@ -69,23 +68,18 @@ void to_public(const Shape &s, ba_tuning *t) {
   t->hist_bins = s.hist_bins;
   t->hist_agg = s.hist_agg;
   t->chains = s.chains;
-  t->lane_chunk = s.lane_chunk;
 }
 
 bool valid_shape(const Shape &s, int kind) {
   if (s.block < 32 || s.block > 1024 || s.block % 32 != 0) return false;
   if (s.ctas_per_sm < 1 || s.ctas_per_sm > 32) return false;
-  if (s.refill < 0 || s.refill > 2) return false;
-  if (s.refill == 2 && kind != BA_KIND_DEGREE) return false;  // lane chunks: degree count only
-  if (s.refill != 0 || kind == BA_KIND_BATCH) {
+  if (s.refill != 0 && s.refill != 1) return false;
+  if (s.refill == 1 || kind == BA_KIND_BATCH) {
     if (s.tile < 64 || s.tile > (1 << 20) || (s.tile & (s.tile - 1)) != 0) return false;
   }
   if (s.hist_bins < 0 || s.hist_bins > 28 * 1024) return false;
   if (s.hist_agg != 0 && s.hist_agg != 1) return false;
   if (s.chains != 1 && s.chains != 2) return false;
-  if (s.lane_chunk != 0 && (s.lane_chunk < 32 || s.lane_chunk > 1024 ||
-                            (s.lane_chunk & (s.lane_chunk - 1)) != 0))
-    return false;
   return true;
 }
 
@@ -101,9 +95,8 @@ ba_status load_file(const char *path, Cache &c) {
   while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
   std::fclose(f);
   // Entries are flat objects {"kind":K,"r32":P,"block":B,"ctas_per_sm":C,"tile":T,
-  // "refill":R,"hist_bins":H,"hist_agg":A[,"chains":N[,"lane_chunk":C]]}; keys are read in
-  // that fixed order (files without "chains" mean one chain per lane, without
-  // "lane_chunk" the default chunk).
+  // "refill":R,"hist_bins":H,"hist_agg":A[,"chains":N]}; keys are read in that fixed order
+  // (files without "chains" mean one chain per lane).
   size_t pos = 0;
   int loaded = 0;
   while ((pos = text.find("{\"kind\"", pos)) != std::string::npos) {
@@ -112,11 +105,10 @@ ba_status load_file(const char *path, Cache &c) {
     const int fields = std::sscanf(
         text.c_str() + pos,
         "{\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-        "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d, "
-        "\"lane_chunk\": %d}",
+        "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d}",
         &kind, &r32, &s.block, &s.ctas_per_sm, &s.tile, &s.refill, &s.hist_bins, &s.hist_agg,
-        &s.chains, &s.lane_chunk);
-    if (fields >= 8 && fields <= 10 &&
+        &s.chains);
+    if ((fields == 8 || fields == 9) &&
         kind >= 0 && kind < kKinds && (r32 == 0 || r32 == 1) && valid_shape(s, kind)) {
       c.tuned[kind][r32] = s;
       c.has_tuned[kind][r32] = true;
@@ -161,8 +153,7 @@ ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out) {
   Shape s = from_public(*t, kind);
   if (!valid_shape(s, kind)) {
     set_error("invalid launch shape (block multiple of 32 <= 1024, tile power of two 64..2^20, "
-              "refill 0, 1 or 2 (2 for the degree count only), hist_bins <= 28672, hist_agg 0 or 1, "
-              "chains 1 or 2, lane_chunk 0 or a power of two 32..1024)");
+              "refill 0 or 1, hist_bins <= 28672, hist_agg 0 or 1, chains 1 or 2)");
     return BA_ERR_INVALID_ARG;
   }
   *out = s;
@@ -228,17 +219,6 @@ std::vector<Shape> candidates(int kind) {
                 out.push_back(s);
               }
           }
-    for (int blk : {512, 1024})
-      for (int ctas : {1, 2})
-        for (int hb : {8192, 12288})
-          for (int chunk : {128, 256, 512})
-            for (int chains : {1, 2}) {
-              if (blk * ctas > 2048 || static_cast<size_t>(hb) * 8 * ctas > 220 * 1024) continue;
-              Shape s;
-              s.block = blk; s.ctas_per_sm = ctas; s.tile = 65536; s.refill = 2;
-              s.hist_bins = hb; s.chains = chains; s.lane_chunk = chunk;
-              out.push_back(s);
-            }
     Shape simple;
     simple.block = 256; simple.ctas_per_sm = 8; simple.tile = 512; simple.refill = 0;
     out.push_back(simple);
@@ -414,10 +394,9 @@ ba_status ba_tune_save(const char *path) {
       const Shape &s = c.tuned[k][r];
       std::fprintf(f,
                    "%s\n  {\"kind\": %d, \"r32\": %d, \"block\": %d, \"ctas_per_sm\": %d, \"tile\": %d, "
-                   "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d, "
-                   "\"lane_chunk\": %d}",
+                   "\"refill\": %d, \"hist_bins\": %d, \"hist_agg\": %d, \"chains\": %d}",
                    firstw ? "" : ",", k, r, s.block, s.ctas_per_sm, s.tile, s.refill, s.hist_bins,
-                   s.hist_agg, s.chains, s.lane_chunk);
+                   s.hist_agg, s.chains);
       firstw = false;
     }
   std::fprintf(f, "\n]}\n");

@@ -143,24 +143,6 @@ def test_offsets_need_one_entry_per_graph_plus_one():
     assert ba.ba_device_allocations() >= 0
 
 
-def test_lane_chunk_shapes_are_degree_only():
-    # refill 2 (lane chunks) exists for the degree count only; its chunk is a power of two
-    for kind in (ba.BA_KIND_GENERATE, ba.BA_KIND_BATCH):
-        with pytest.raises(ba.BAError) as e:
-            ba.ba_set_tuning(kind, {"refill": 2})
-        assert e.value.status == ba.BA_ERR_INVALID_ARG
-    for bad in ({"refill": 2, "lane_chunk": 48}, {"refill": 2, "lane_chunk": 16},
-                {"refill": 2, "lane_chunk": 2048}):
-        with pytest.raises(ba.BAError):
-            ba.ba_set_tuning(ba.BA_KIND_DEGREE, bad)
-    try:
-        ba.ba_set_tuning(ba.BA_KIND_DEGREE, {"refill": 2, "lane_chunk": 256, "chains": 1})
-        t = ba.ba_get_tuning(ba.BA_KIND_DEGREE)
-        assert (t["refill"], t["lane_chunk"], t["chains"]) == (2, 256, 1)
-    finally:
-        ba.ba_set_tuning(ba.BA_KIND_DEGREE, None)
-
-
 def test_probe_argument_rules():
     with pytest.raises(ba.BAError) as e:
         ba.ba_probe_hash(1, 0, 100, 1, None, stream=0)                 # no sink

@@ -59,16 +59,6 @@ SHAPES = [
     {"refill": 1, "block": 256, "ctas_per_sm": 2, "tile": 512, "hist_bins": 4096, "chains": 2},
     {"refill": 1, "block": 512, "ctas_per_sm": 1, "tile": 16384, "hist_bins": 8192, "hist_agg": 1,
      "chains": 2},
-    # lane chunks
-    {"refill": 2, "block": 32, "ctas_per_sm": 4, "tile": 64, "hist_bins": 7, "lane_chunk": 32},
-    {"refill": 2, "block": 256, "ctas_per_sm": 2, "tile": 512, "hist_bins": 0, "lane_chunk": 64},
-    {"refill": 2, "block": 512, "ctas_per_sm": 2, "tile": 4096, "hist_bins": 8192},
-    {"refill": 2, "block": 1024, "ctas_per_sm": 1, "tile": 1024, "hist_bins": 20480,
-     "lane_chunk": 1024},
-    {"refill": 2, "block": 128, "ctas_per_sm": 8, "tile": 256, "hist_bins": 1000, "chains": 2,
-     "lane_chunk": 128},
-    {"refill": 2, "block": 512, "ctas_per_sm": 1, "tile": 65536, "hist_bins": 12288, "chains": 2,
-     "lane_chunk": 256},
 ]
 
 
@@ -84,8 +74,8 @@ def test_counts_do_not_depend_on_launch_shape(ba, shape):
     np.testing.assert_array_equal(got.cpu().numpy().astype(np.uint64), want)
 
 
-SCHEDULERS = [None, {"refill": 1, "chains": 1}, {"refill": 2, "chains": 1, "lane_chunk": 64},
-              {"refill": 2, "chains": 2, "block": 128, "tile": 256, "hist_bins": 300}]
+SCHEDULERS = [None, {"refill": 1, "chains": 1},
+              {"refill": 1, "chains": 2, "block": 128, "tile": 256, "hist_bins": 300}]
 
 
 @pytest.mark.parametrize("shape", SCHEDULERS, ids=str)
@@ -118,6 +108,21 @@ def test_seed_cliques_and_ranges_across_schedulers(ba, shape, seed, n, d, n0, a,
         ba.ba_set_tuning(ba.BA_KIND_DEGREE, None)
     np.testing.assert_array_equal(got.cpu().numpy().astype(np.uint64),
                                   opar.degree_count_range(seed, n, d, n0, a, b, limit))
+
+
+@pytest.mark.parametrize("shape", SCHEDULERS, ids=str)
+def test_positions_near_2_to_the_61(ba, shape):
+    seed, n, d = 97, 2**40, 2**20
+    m = n * d
+    a, b = m - 30_000, m
+    try:
+        if shape is not None:
+            ba.ba_set_tuning(ba.BA_KIND_DEGREE, shape)
+        got = _counts(ba, seed, n, d, 0, a, b, 1000)
+    finally:
+        ba.ba_set_tuning(ba.BA_KIND_DEGREE, None)
+    np.testing.assert_array_equal(got.cpu().numpy().astype(np.uint64),
+                                  oracle.degree_count_range(seed, n, d, 0, a, b, 1000))
 
 
 def test_large_workload_prefix_partition_and_degree_sum(ba):

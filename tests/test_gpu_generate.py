@@ -126,6 +126,17 @@ def test_64_bit_positions_other_d_and_seed_cliques(ba, seed, n, d, n0, shape):
     _with_shape(ba, shape, run)
 
 
+@pytest.mark.parametrize("seed,n,d", [(91, 2**40, 2**20), (93, 2**41 + 7, 2**21 - 3),
+                                      (95, 3 * 2**60 // 2**20, 2**20 - 1)])
+def test_positions_up_to_2_to_the_62(ba, seed, n, d):
+    # every 32-bit partial product of the 64-bit-position hash is non-trivial here (the
+    # high half of r reaches 2^29 and beyond)
+    m = n * d
+    for a, b in [(m - 20_000, m), (m // 2 - 5_000, m // 2 + 5_000), (2**33, 2**33 + 5_000)]:
+        np.testing.assert_array_equal(_gpu(ba, seed, n, d, 0, a, b),
+                                      oracle.edges_range(seed, n, d, 0, a, b))
+
+
 def test_host_output_matches_device_output(ba):
     g = W.PLAIN_SMALL
     host = torch.empty((g.m, 2), dtype=torch.int64).pin_memory()
