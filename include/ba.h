@@ -354,6 +354,7 @@ typedef struct ba_server_config {
 typedef struct ba_server_stats {
     uint64_t submitted, admitted, completed, released, rejected_busy;
     uint64_t ticks, edges_done, bytes_in_use, queue_depth, active;
+    uint64_t cancelled;
 } ba_server_stats;
 
 /* Request states reported by ba_server_poll. */
@@ -392,6 +393,13 @@ ba_status ba_server_copy_result(ba_server *server, uint64_t ticket, int64_t *dst
 
 /* Frees a finished request's buffer, returning its bytes to the budget. */
 ba_status ba_server_release(ba_server *server, uint64_t ticket);
+
+/* Withdraws a request that is still QUEUED (waiting for admission): it is dropped without
+ * any device work and its ticket becomes unknown (a later poll, wait or release of it gives
+ * BA_ERR_NOT_FOUND).  A RUNNING request cannot be withdrawn -- its chunks may already be on
+ * the GPU -- and a DONE or FAILED one is released instead: both give BA_ERR_BUSY.  Unknown
+ * tickets give BA_ERR_NOT_FOUND.  Counted in ba_server_stats.cancelled. */
+ba_status ba_server_cancel(ba_server *server, uint64_t ticket);
 
 ba_status ba_server_stats_get(ba_server *server, ba_server_stats *stats);
 

@@ -57,7 +57,7 @@ class ba_server_config(ctypes.Structure):
 class ba_server_stats(ctypes.Structure):
     _fields_ = [(k, _u64) for k in ("submitted", "admitted", "completed", "released",
                                     "rejected_busy", "ticks", "edges_done", "bytes_in_use",
-                                    "queue_depth", "active")]
+                                    "queue_depth", "active", "cancelled")]
 
 
 def _sig(name, restype, *argtypes):
@@ -107,6 +107,7 @@ _sig("ba_server_wait", ctypes.c_int, _vp, _u64, _i64)
 _sig("ba_server_result", ctypes.c_int, _vp, _u64, ctypes.POINTER(_vp), ctypes.POINTER(_u64))
 _sig("ba_server_copy_result", ctypes.c_int, _vp, _u64, _vp, _vp)
 _sig("ba_server_release", ctypes.c_int, _vp, _u64)
+_sig("ba_server_cancel", ctypes.c_int, _vp, _u64)
 _sig("ba_server_stats_get", ctypes.c_int, _vp, ctypes.POINTER(ba_server_stats))
 _sig("ba_server_destroy", ctypes.c_int, _vp)
 
@@ -377,6 +378,11 @@ def ba_server_result(server: int, ticket: int) -> tuple[int, int]:
 
 def ba_server_release(server: int, ticket: int) -> None:
     _check(_lib.ba_server_release(server, ticket), "ba_server_release")
+
+
+def ba_server_cancel(server: int, ticket: int) -> None:
+    """Withdraws a request that is still waiting for admission."""
+    _check(_lib.ba_server_cancel(server, ticket), "ba_server_cancel")
 
 
 def ba_server_stats_get(server: int) -> dict:

@@ -490,6 +490,37 @@ ba_status ba_server_release(ba_server *s, uint64_t ticket) {
   return BA_OK;
 }
 
+ba_status ba_server_cancel(ba_server *s, uint64_t ticket) {
+  if (!s) {
+    set_error("NULL server");
+    return BA_ERR_INVALID_ARG;
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+      set_error("unknown ticket");
+      return BA_ERR_NOT_FOUND;
+    }
+    if (it->second.state != BA_REQ_QUEUED) {
+      set_error(it->second.state == BA_REQ_RUNNING
+                    ? "request already admitted: wait for it, then release it"
+                    : "request finished: release it");
+      return BA_ERR_BUSY;
+    }
+    // a QUEUED request holds no arena space and has no work on the device
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+      if (*q == ticket) {
+        s->queue.erase(q);
+        break;
+      }
+    s->reqs.erase(it);
+    s->stats.cancelled++;
+  }
+  s->cv.notify_all();
+  return BA_OK;
+}
+
 ba_status ba_server_stats_get(ba_server *s, ba_server_stats *out) {
   if (!s || !out) {
     set_error("NULL argument");

@@ -143,6 +143,13 @@ def test_offsets_need_one_entry_per_graph_plus_one():
     assert ba.ba_device_allocations() >= 0
 
 
+def test_server_calls_reject_a_null_server():
+    for call in (lambda: ba.ba_server_cancel(None, 1), lambda: ba.ba_server_release(None, 1)):
+        with pytest.raises(ba.BAError) as e:
+            call()
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+
+
 def test_probe_argument_rules():
     with pytest.raises(ba.BAError) as e:
         ba.ba_probe_hash(1, 0, 100, 1, None, stream=0)                 # no sink

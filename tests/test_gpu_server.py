@@ -177,3 +177,39 @@ def test_poisson_trace_sampled_one_percent_exact_against_oracle(ba):
             np.testing.assert_array_equal(
                 got, opar.edges_range(r.graph.seed, r.graph.n, r.graph.d, 0,
                                       r.edge_begin + lo, r.edge_begin + hi))
+
+
+def test_cancel_withdraws_only_queued_requests(ba):
+    # a budget of one request's output: the second and third requests queue behind the first
+    n, d = 2**22, 4
+    big = (1, n, d, 0, 0, 4 * 2**20)
+    srv = ba.ba_server_create(memory_budget_bytes=16 * 4 * 2**20, chunk_edges=1 << 18,
+                              max_active=8)
+    try:
+        t1 = ba.ba_server_submit(srv, *big)
+        ba.ba_server_wait(srv, t1, 60_000)           # done, its buffer still held
+        t2 = ba.ba_server_submit(srv, 2, n, d, 0, 100, 100 + 2**20)
+        t3 = ba.ba_server_submit(srv, 3, n, d, 0, 7, 7 + 2**20)
+        state2, _ = ba.ba_server_poll(srv, t2)
+        assert state2 == ba.BA_REQ_QUEUED            # no room until t1 is released
+        ba.ba_server_cancel(srv, t2)
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_poll(srv, t2)
+        assert e.value.status == ba.BA_ERR_NOT_FOUND
+        with pytest.raises(ba.BAError) as e:         # finished: released, not withdrawn
+            ba.ba_server_cancel(srv, t1)
+        assert e.value.status == ba.BA_ERR_BUSY
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_server_cancel(srv, 10**9)
+        assert e.value.status == ba.BA_ERR_NOT_FOUND
+        r1 = ba.server_result_tensor(srv, t1)
+        ba.ba_server_release(srv, t1)                # frees room: t3 runs now
+        ba.ba_server_wait(srv, t3, 60_000)
+        r3 = ba.server_result_tensor(srv, t3)
+        ba.ba_server_release(srv, t3)
+        st = ba.ba_server_stats_get(srv)
+        assert st["cancelled"] == 1 and st["completed"] == 2 and st["bytes_in_use"] == 0
+    finally:
+        ba.ba_server_destroy(srv)
+    assert torch.equal(r1, _plain(ba, *big))
+    assert torch.equal(r3, _plain(ba, 3, n, d, 0, 7, 7 + 2**20))
