@@ -133,6 +133,26 @@ ba_status ba_degree_count_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t 
                                 uint64_t node_limit, uint64_t *counts_dev,
                                 int accumulate, void *stream);
 
+/*
+ * Checked launch (a debug aid in place of a sanitizer): ba_generate_edges with every
+ * output store compared with a capacity the caller states, out_capacity_edges edges
+ * (16-byte pairs) at out_dev.  A store to a slot at or beyond the capacity is not made;
+ * the lowest such slot is kept in *status_dev (device, 8 bytes, caller-owned), which the
+ * call first sets to UINT64_MAX ("no violation").  The kernel never traps: read the result
+ * with ba_check_status.  Same arguments and errors as ba_generate_edges otherwise; always
+ * the refill kernel with the tuned shape; the stored slots hold the same bits as an
+ * unchecked call.  Asynchronous on `stream`.
+ */
+ba_status ba_generate_edges_checked(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                    uint64_t edge_begin, uint64_t edge_end, int64_t *out_dev,
+                                    uint64_t out_capacity_edges, uint64_t *status_dev,
+                                    void *stream);
+
+/* Synchronises `stream`, then reads a checked launch's status word: BA_OK when no store
+ * went beyond the capacity, else BA_ERR_CUDA with the first offending slot in
+ * ba_last_error_message(). */
+ba_status ba_check_status(const uint64_t *status_dev, void *stream);
+
 /* ----------------------------------------------------------------------- variants -- */
 
 /* Variants of the graph, as bit flags (0 = the graph of ba_generate_edges):
@@ -313,6 +333,22 @@ ba_status ba_generate_batch(const ba_graph_desc *descs, int32_t G,
 ba_status ba_generate_batch_noalloc(const ba_graph_desc *descs, int32_t G,
                                     const int64_t *offsets_host, int64_t *out_dev,
                                     void *stream);
+
+/* ------------------------------------------------------------ work-bound counter -- */
+
+/*
+ * Section 2's work bound, counted on the device: hist_dev[k] (+)= the number of edges i in
+ * [edge_begin, edge_end) whose second end point took k draws h(r) in the chain of Fig. 1
+ * (from position 2i+1 until the position is even or, with a seed clique, below 2 m0; 0 for
+ * the seed edges themselves), for k < bins-1; hist_dev[bins-1] counts the chains of bins-1
+ * draws or more.  bins in 2..1024; hist_dev (device, caller-owned, 8-byte aligned) holds
+ * bins uint64 counters, overwritten unless accumulate != 0.  One thread per edge with the
+ * plain C form of the hash: a measurement, not a hot path.  Asynchronous on `stream`.
+ * Errors as ba_degree_count_range, plus BA_ERR_INVALID_ARG for bins or hist_dev.
+ */
+ba_status ba_chain_lengths(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                           uint64_t edge_begin, uint64_t edge_end, uint32_t bins,
+                           uint64_t *hist_dev, int accumulate, void *stream);
 
 /* ---------------------------------------------------------------- roofline probes -- */
 

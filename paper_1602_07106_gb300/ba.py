@@ -98,6 +98,11 @@ _sig("ba_generate_batch", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp
 _sig("ba_generate_batch_noalloc", ctypes.c_int, ctypes.POINTER(ba_graph_desc), _i32, _vp, _vp,
      _vp)
 _sig("ba_device_allocations", _u64)
+_sig("ba_generate_edges_checked", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _vp, _u64, _vp,
+     _vp)
+_sig("ba_check_status", ctypes.c_int, _vp, _vp)
+_sig("ba_chain_lengths", ctypes.c_int, _u64, _u64, _u32, _u64, _u64, _u64, _u32, _vp, ctypes.c_int,
+     _vp)
 _sig("ba_probe_hash", ctypes.c_int, _u64, _u64, _u64, _i32, _vp, _vp)
 _sig("ba_probe_write", ctypes.c_int, _vp, _u64, _vp)
 _sig("ba_server_create", ctypes.c_int, ctypes.POINTER(ba_server_config), ctypes.POINTER(_vp))
@@ -321,6 +326,29 @@ def ba_generate_batch_noalloc(graphs, out, offsets=None, stream=None) -> None:
     keep, off = _offsets_arg(offsets, G)
     _check(_lib.ba_generate_batch_noalloc(arr, G, off, _ptr(out), _stream(stream)),
            "ba_generate_batch_noalloc")
+
+
+def ba_chain_lengths(seed, n, d, n0, edge_begin, edge_end, bins, hist, accumulate=False,
+                     stream=None) -> None:
+    """Histogram of the chain lengths (draws per edge) of edges [edge_begin, edge_end) into
+    the int64 device tensor hist (bins entries; the last one counts bins-1 draws or more)."""
+    _check(_lib.ba_chain_lengths(seed, n, d, n0, edge_begin, edge_end, bins, _ptr(hist),
+                                 int(bool(accumulate)), _stream(stream)), "ba_chain_lengths")
+
+
+def ba_generate_edges_checked(seed, n, d, n0, edge_begin, edge_end, out, capacity, status,
+                              stream=None) -> None:
+    """ba_generate_edges with every store checked against `capacity` edges of `out`;
+    `status` is a one-element int64 device tensor read by ba_check_status."""
+    _check(_lib.ba_generate_edges_checked(seed, n, d, n0, edge_begin, edge_end, _ptr(out),
+                                          capacity, _ptr(status), _stream(stream)),
+           "ba_generate_edges_checked")
+
+
+def ba_check_status(status, stream=None) -> None:
+    """Raises BAError (BA_ERR_CUDA) if the checked launch behind `status` found a store
+    beyond its capacity."""
+    _check(_lib.ba_check_status(_ptr(status), _stream(stream)), "ba_check_status")
 
 
 def ba_device_allocations() -> int:

@@ -229,6 +229,54 @@ ba_status ba_generate_edges(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
   return launch_generate(g, out_dev, shape, static_cast<unsigned long long *>(scratch.ptr), s);
 }
 
+ba_status ba_generate_edges_checked(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
+                                    uint64_t edge_begin, uint64_t edge_end, int64_t *out_dev,
+                                    uint64_t out_capacity_edges, uint64_t *status_dev,
+                                    void *stream) {
+  set_error("");
+  uint64_t m = 0;
+  ba_status st = check_range(n, d, n0, edge_begin, edge_end, &m);
+  if (st != BA_OK) return st;
+  if (status_dev == nullptr || (reinterpret_cast<uintptr_t>(status_dev) & 7) != 0) {
+    set_error("status must be a non-NULL, 8-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(status_dev, 0xff, sizeof(uint64_t), s);  // no violation yet
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (edge_begin == edge_end) return BA_OK;
+  if (out_dev == nullptr || (reinterpret_cast<uintptr_t>(out_dev) & 15) != 0) {
+    set_error("out must be a non-NULL, 16-byte aligned device pointer");
+    return BA_ERR_INVALID_ARG;
+  }
+  const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
+  const Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  StreamScratch scratch;
+  st = scratch.alloc(sizeof(unsigned long long), s);
+  if (st != BA_OK) return st;
+  return launch_generate_checked(g, out_dev, out_capacity_edges,
+                                 reinterpret_cast<unsigned long long *>(status_dev), shape,
+                                 static_cast<unsigned long long *>(scratch.ptr), s);
+}
+
+ba_status ba_check_status(const uint64_t *status_dev, void *stream) {
+  set_error("");
+  if (status_dev == nullptr) {
+    set_error("NULL status");
+    return BA_ERR_INVALID_ARG;
+  }
+  uint64_t v = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, status_dev, sizeof v, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the check status");
+  if (v == ~0ull) return BA_OK;
+  set_error(("device check: a store to output slot " + std::to_string(v) +
+             " (edge offset from the start of out) was beyond the declared capacity; "
+             "it and every later slot were skipped").c_str());
+  return BA_ERR_CUDA;
+}
+
 ba_status ba_generate_edges32(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
                               uint64_t edge_begin, uint64_t edge_end, int32_t *out_dev,
                               void *stream) {

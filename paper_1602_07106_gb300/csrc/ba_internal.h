@@ -18,6 +18,10 @@ struct SchedParams {
   uint32_t total_warps;          // warps in the grid (first tile of warp w is w)
   uint32_t hist_agg;             // degree kernel: warp-aggregate histogram increments
   uint32_t pad;
+  // checked launches only: output slots [0, out_cap) exist; a store to a slot beyond them
+  // is skipped and the lowest such slot is kept in *status (atomicMin)
+  uint64_t out_cap;
+  unsigned long long *status;
 };
 
 // Graph table of a batched launch (device pointers).
@@ -84,6 +88,10 @@ ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t
 // from its old target to its new one.  d <= 1024.
 ba_status launch_count_rejections(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                                   cudaStream_t stream, bool no_loops);
+// launch_generate with every output store checked against out_cap (edges): see SchedParams.
+ba_status launch_generate_checked(const GraphDev &g, int64_t *out, uint64_t out_cap,
+                                  unsigned long long *status, const Shape &s,
+                                  unsigned long long *counter, cudaStream_t stream);
 ba_status launch_batch(const BatchTable &tab, uint64_t total_tiles, bool r32, bool has_seed,
                        int64_t *out, const Shape &s, unsigned long long *counter,
                        cudaStream_t stream);

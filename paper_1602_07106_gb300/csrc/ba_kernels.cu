@@ -95,11 +95,25 @@ __device__ __forceinline__ void copy_graph(GraphDev *dst, const GraphDev *src) {
 // Writes the finished chunk [base, base+len) of the staging ring: lane j of the warp
 // handles edges base+j, base+j+32, ... so each warp store covers 512 contiguous bytes (256
 // with Narrow int32 pairs).
-template <class RT, bool HasSeed, bool Narrow = false>
+// Checked: a store to slot out_cap or beyond is skipped and the lowest such slot is kept in
+// *status (the checked launch; the slot bound comes from the caller, not from the range).
+template <class RT, bool HasSeed, bool Narrow = false, bool Checked = false>
 __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint32_t len,
-                                           const GraphDev &g, int64_t *__restrict__ out) {
+                                           const GraphDev &g, int64_t *__restrict__ out,
+                                           uint64_t out_cap = 0,
+                                           unsigned long long *status = nullptr) {
   __syncwarp();
   const uint64_t out0 = g.out_edge + (base - g.begin);
+  // false (and the slot recorded) when slot k does not exist
+  [[maybe_unused]] auto slot_ok = [&](uint64_t k) {
+    if constexpr (Checked) {
+      if (k >= out_cap) {
+        atomicMin(status, static_cast<unsigned long long>(k));
+        return false;
+      }
+    }
+    return true;
+  };
   if constexpr (sizeof(RT) == 4) {
     // 32-bit positions: i < 2^31 and every node ID < 2^32, so the pairs are built from
     // 32-bit words (high words zero).
@@ -122,6 +136,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         else return __umulhi(x, dv.m32) >> np2_shift;
       };
       auto put = [&](uint32_t j, uint32_t u, uint32_t v) {
+        if (!slot_ok(out0 + j)) return;
         if constexpr (Narrow)
           __stcs(dst2 + j, make_int2(static_cast<int>(u), static_cast<int>(v)));
         else
@@ -179,7 +194,8 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     const uint32_t l = g.div.l;
 #pragma unroll 4
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32)
-      store_pair<Narrow>(out, out0 + j, (base + j) >> l, static_cast<uint64_t>(stage[j]) >> (l + 1));
+      if (slot_ok(out0 + j))
+        store_pair<Narrow>(out, out0 + j, (base + j) >> l, static_cast<uint64_t>(stage[j]) >> (l + 1));
   } else {
     for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
       const uint64_t i = base + j;
@@ -191,7 +207,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         u = source_of<RT, HasSeed>(i, g);
         v = target_of<RT, HasSeed>(stage[j], g);
       }
-      store_pair<Narrow>(out, out0 + j, u, v);
+      if (slot_ok(out0 + j)) store_pair<Narrow>(out, out0 + j, u, v);
     }
   }
   __syncwarp();
@@ -208,7 +224,7 @@ constexpr uint32_t kChunk = 256;
 // each lane has K independent hash chains in flight.  The hash is one long dependency
 // chain of integer multiplies and shifts; a second chain per lane hides its latency.
 template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlain,
-          int K = 1>
+          int K = 1, bool Checked = false>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
                   int64_t *__restrict__ out) {
@@ -247,7 +263,8 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     const RT r0 = static_cast<RT>(2 * base + 1);
     auto flush = [&](uint32_t from, uint32_t count) {
       // ring entries from..from+count-1 are contiguous: a chunk never wraps the ring
-      flush_tile<RT, HasSeed, Narrow>(ring + (from & (kRing - 1)), base + from, count, g, out);
+      flush_tile<RT, HasSeed, Narrow, Checked>(ring + (from & (kRing - 1)), base + from, count, g,
+                                               out, sp.out_cap, sp.status);
     };
 
     // Chain c of this lane: edge base+o[c] at position r[c] while busy[c].
@@ -628,12 +645,13 @@ ba_status check_launch(const char *what) {
   return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
 }
 
-template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlainGen>
+template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlainGen, bool Checked = false>
 ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, uint64_t out_cap = 0,
+                     unsigned long long *status = nullptr) {
   const uint64_t len = g.end - g.begin;
   const int block = s.block;
-  if constexpr (Draw::kPlain) {  // the simple kernel draws h(r) only
+  if constexpr (Draw::kPlain && !Checked) {  // the simple kernel draws h(r) only
     if (s.refill == 0) {
       int grid = 0;
       ba_status st = persistent_grid(k_generate_simple<RT, HasSeed, Narrow>, block, 0,
@@ -647,8 +665,8 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
                       (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
-  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, false, Narrow, Draw, 2>
-                              : k_generate_refill<RT, HasSeed, false, Narrow, Draw, 1>;
+  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, false, Narrow, Draw, 2, Checked>
+                              : k_generate_refill<RT, HasSeed, false, Narrow, Draw, 1, Checked>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   // Tiles of the tuned size, halved (down to 256) until every warp of a full grid has
@@ -666,6 +684,8 @@ ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned l
   sp.hist_agg = static_cast<uint32_t>(s.hist_agg);
   grid = static_cast<int>(std::min<uint64_t>(grid, (sp.num_tiles + warps - 1) / warps));
   sp.total_warps = static_cast<uint32_t>(grid) * warps;
+  sp.out_cap = out_cap;
+  sp.status = status;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   kernel<<<grid, block, smem, stream>>>(g, BatchTable{}, sp, out);
@@ -764,6 +784,20 @@ ba_status launch_generate(const GraphDev &g, int64_t *out, const Shape &s,
                        : generate_t<uint32_t, false, false>(g, out, s, counter, stream);
   return seed ? generate_t<uint64_t, true, false>(g, out, s, counter, stream)
               : generate_t<uint64_t, false, false>(g, out, s, counter, stream);
+}
+
+ba_status launch_generate_checked(const GraphDev &g, int64_t *out, uint64_t out_cap,
+                                  unsigned long long *status, const Shape &shape,
+                                  unsigned long long *counter, cudaStream_t stream) {
+  g_kernel_count = 0;
+  Shape s = shape;
+  s.refill = 1;  // the checks live in the refill kernel's store path
+  const bool r32 = g.end <= (1ull << 31);
+  if (g.m0 > 0)
+    return r32 ? generate_t<uint32_t, true, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status)
+               : generate_t<uint64_t, true, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status);
+  return r32 ? generate_t<uint32_t, false, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status)
+             : generate_t<uint64_t, false, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status);
 }
 
 namespace {

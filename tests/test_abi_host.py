@@ -143,6 +143,28 @@ def test_offsets_need_one_entry_per_graph_plus_one():
     assert ba.ba_device_allocations() >= 0
 
 
+def test_checked_launch_argument_rules():
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_check_status(None, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:                       # no status word
+        ba.ba_generate_edges_checked(1, 10, 2, 0, 0, 5, 0x1000, 5, None, stream=0)
+    assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:                       # range beyond m, checked first
+        ba.ba_generate_edges_checked(1, 10, 2, 0, 0, 21, 0x1000, 21, 0x2000, stream=0)
+    assert e.value.status == ba.BA_ERR_RANGE
+
+
+def test_chain_lengths_argument_rules():
+    for bins, hist in ((1, 0x1000), (1025, 0x1000), (8, None), (8, 0x1004)):
+        with pytest.raises(ba.BAError) as e:
+            ba.ba_chain_lengths(1, 10, 2, 0, 0, 5, bins, hist, stream=0)
+        assert e.value.status == ba.BA_ERR_INVALID_ARG
+    with pytest.raises(ba.BAError) as e:
+        ba.ba_chain_lengths(1, 10, 2, 0, 0, 21, 8, 0x1000, stream=0)
+    assert e.value.status == ba.BA_ERR_RANGE
+
+
 def test_server_calls_reject_a_null_server():
     for call in (lambda: ba.ba_server_cancel(None, 1), lambda: ba.ba_server_release(None, 1)):
         with pytest.raises(ba.BAError) as e:
