@@ -252,11 +252,30 @@ def reference_arm(args):
                              f"degree-counted (2 x {sample} edge generations)",
                    "parallelism": f"{cores} host processes"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": host_cpu_model(),
                          "sample": f"edges [0, {sample}) generated and degree-counted per step"},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def host_cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer/part on Arm)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    parts = [f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part", "CPU variant") if k in fields]
+    return f"{platform.machine()} ({', '.join(parts)})" if parts else platform.machine()
 
 
 def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
@@ -286,6 +305,7 @@ def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
     oracle.edges_range(sm.seed, sm.n, sm.d, 0, 0, sm.m)
     t_rc = time.perf_counter() - t0
     return {"value": 2 * sample_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "cpu_model": host_cpu_model(),
             "sample": f"edges [0, {sample_edges}) of n=2^27 d=16 seed=42: edge list + degree "
                       f"count of nodes < 1e5, {dt:.1f} s wall on {cores} processes",
             "one_core_small_workload": {
@@ -510,8 +530,12 @@ def gpu_arm(args):
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
+        d2h = 16 * m_shard + 8 * NODE_LIMIT
         e2e = {"value": edges_per_step * args.e2e_steps / dt, "unit": "edges/s",
-               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 16 * m_shard + 8 * NODE_LIMIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+               "d2h_gbs": d2h * args.e2e_steps / dt / 1e9,
+               "bound_by": "the device-to-host copy of the 34.4 GB edge list (d2h_gbs); the "
+                           "kernels take ~15 ms of each step",
                "host_buffer": "pinned" if pinned else "pageable", "steps": args.e2e_steps,
                "ms_per_step": 1000 * dt / args.e2e_steps}
         del host_out

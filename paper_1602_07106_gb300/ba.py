@@ -51,7 +51,8 @@ class ba_graph_desc(ctypes.Structure):
 
 class ba_server_config(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", _u64), ("chunk_edges", _u64), ("max_active", _i32),
-                ("max_inflight_ticks", _i32), ("device", _i32), ("max_queued", _i32)]
+                ("max_inflight_ticks", _i32), ("device", _i32), ("max_queued", _i32),
+                ("tick_edges", _u64)]
 
 
 class ba_server_stats(ctypes.Structure):
@@ -370,9 +371,9 @@ def ba_probe_write(dst, nbytes=None, stream=None) -> None:
 
 
 def ba_server_create(memory_budget_bytes=0, chunk_edges=0, max_active=0, max_inflight_ticks=0,
-                     device=-1, max_queued=0) -> int:
+                     device=-1, max_queued=0, tick_edges=0) -> int:
     cfg = ba_server_config(memory_budget_bytes, chunk_edges, max_active, max_inflight_ticks,
-                           device, max_queued)
+                           device, max_queued, tick_edges)
     srv = _vp()
     _check(_lib.ba_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "ba_server_create")
     return srv.value

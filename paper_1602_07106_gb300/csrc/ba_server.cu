@@ -174,14 +174,28 @@ void prepare_tick(ba_server *s, TickSlot &slot, TickPlan &plan) {
   pre[0][0] = pre[1][0] = 0;
   plan.shape[0] = shape_for(BA_KIND_BATCH, true);
   plan.shape[1] = shape_for(BA_KIND_BATCH, false);
+  // With a tick budget, the requests with the least work left go first and the budget is
+  // handed out in that order (the first always gets work); the rest wait for a later tick.
+  if (s->cfg.tick_edges > 0)
+    std::stable_sort(s->running.begin(), s->running.end(), [&](uint64_t x, uint64_t y) {
+      const Request &rx = s->reqs[x], &ry = s->reqs[y];
+      return rx.len - rx.cursor < ry.len - ry.cursor;
+    });
+  std::vector<uint64_t> take(s->running.size(), 0);  // edges of each request in this tick
+  uint64_t budget = s->cfg.tick_edges > 0 ? s->cfg.tick_edges : ~0ull;
+  for (size_t k = 0; k < s->running.size() && budget > 0; ++k) {
+    const Request &r = s->reqs[s->running[k]];
+    take[k] = std::min({r.len - r.cursor, s->cfg.chunk_edges, budget});
+    budget -= take[k];
+  }
   // This tick's work per position path, then tiles sized to it (a light tick still spreads
   // over the GPU; see adapt_tile).
   uint64_t work[2] = {0, 0};
-  for (uint64_t ticket : s->running) {
-    const Request &r = s->reqs[ticket];
+  for (size_t k = 0; k < s->running.size(); ++k) {
+    if (take[k] == 0) continue;
+    const Request &r = s->reqs[s->running[k]];
     const uint64_t a = r.desc.edge_begin + r.cursor;
-    const uint64_t b = std::min(r.desc.edge_begin + r.len, a + s->cfg.chunk_edges);
-    work[b <= (1ull << 31) ? 0 : 1] += b - a;
+    work[a + take[k] <= (1ull << 31) ? 0 : 1] += take[k];
   }
   plan.shape[0].tile = adapt_tile(work[0], plan.shape[0]);
   plan.shape[1].tile = adapt_tile(work[1], plan.shape[1]);
@@ -190,10 +204,15 @@ void prepare_tick(ba_server *s, TickSlot &slot, TickPlan &plan) {
   std::vector<uint64_t> still;
   slot.completing.clear();
   uint64_t edges = 0;
-  for (uint64_t ticket : s->running) {
+  for (size_t k = 0; k < s->running.size(); ++k) {
+    const uint64_t ticket = s->running[k];
     Request &r = s->reqs[ticket];
+    if (take[k] == 0) {  // no budget left in this tick
+      still.push_back(ticket);
+      continue;
+    }
     const uint64_t a = r.desc.edge_begin + r.cursor;
-    const uint64_t b = std::min(r.desc.edge_begin + r.len, a + s->cfg.chunk_edges);
+    const uint64_t b = a + take[k];
     const int path = b <= (1ull << 31) ? 0 : 1;
     GraphDev g = make_graph_dev(r.desc.seed, r.desc.n, r.desc.d, r.desc.n0, a, b);
     g.out_edge = r.arena_off + r.cursor;
