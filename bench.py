@@ -770,7 +770,11 @@ def serving(args, ba, torch, plain_rate):
     want_buf = torch.empty((big, 2), dtype=torch.int64, device="cuda")
     check_stream = torch.cuda.Stream()
     sample_exact = 0
-    srv = ba.ba_server_create(memory_budget_bytes=96 << 30, chunk_edges=1 << 24, max_active=256)
+    # chunks up to 2^27 edges per request, and at a light load at most 2^27 edges per tick,
+    # handed out shortest request first (the configuration with the lowest p99 that keeps
+    # the saturated rate: a sweep of chunk and tick sizes on this trace)
+    srv = ba.ba_server_create(memory_budget_bytes=96 << 30, chunk_edges=1 << 27, max_active=256,
+                              tick_edges=1 << 27)
     lat = []
     edges = 0
     try:
@@ -845,6 +849,8 @@ def serving(args, ba, torch, plain_rate):
     lat.sort()
     return {"workload": f"Poisson 2000 req/s for {args.serve_seconds:g} s ({len(trace)} requests; "
                         "n log-uniform 1e4..1e9, d in {2,4,8,16,32}, 1e4..1e8 edges each)",
+            "server": {"chunk_edges": 1 << 27, "tick_edges": 1 << 27, "max_active": 256,
+                       "memory_budget_bytes": 96 << 30},
             "sample_checked": len(sample), "sample_exact": sample_exact,
             "sample_check": "seeded 1 % of the requests, copied out before release and compared "
                             "on the GPU with ba_generate_edges on the same range",

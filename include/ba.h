@@ -386,8 +386,9 @@ typedef struct ba_server_config {
     int32_t device;                /* CUDA device ordinal (-1 = current) */
     int32_t max_queued;            /* requests waiting for admission (0 = no limit) */
     uint64_t tick_edges;           /* edges per tick over all requests, handed out
-                                      shortest remaining request first (0 = no limit:
-                                      every running request gets its chunk each tick) */
+                                      shortest remaining request first, while no request
+                                      waits for admission (0 = no limit: every running
+                                      request gets its chunk each tick) */
 } ba_server_config;
 
 typedef struct ba_server_stats {

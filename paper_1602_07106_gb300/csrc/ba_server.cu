@@ -176,13 +176,17 @@ void prepare_tick(ba_server *s, TickSlot &slot, TickPlan &plan) {
   plan.shape[1] = shape_for(BA_KIND_BATCH, false);
   // With a tick budget, the requests with the least work left go first and the budget is
   // handed out in that order (the first always gets work); the rest wait for a later tick.
-  if (s->cfg.tick_edges > 0)
+  // The budget holds only while no request waits for admission: it bounds the tick a short
+  // request arriving at a light load waits behind, and when requests queue up (a saturated
+  // server) full ticks keep the per-tick overhead small.
+  const bool budgeted = s->cfg.tick_edges > 0 && s->queue.empty();
+  if (budgeted)
     std::stable_sort(s->running.begin(), s->running.end(), [&](uint64_t x, uint64_t y) {
       const Request &rx = s->reqs[x], &ry = s->reqs[y];
       return rx.len - rx.cursor < ry.len - ry.cursor;
     });
   std::vector<uint64_t> take(s->running.size(), 0);  // edges of each request in this tick
-  uint64_t budget = s->cfg.tick_edges > 0 ? s->cfg.tick_edges : ~0ull;
+  uint64_t budget = budgeted ? s->cfg.tick_edges : ~0ull;
   for (size_t k = 0; k < s->running.size() && budget > 0; ++k) {
     const Request &r = s->reqs[s->running[k]];
     take[k] = std::min({r.len - r.cursor, s->cfg.chunk_edges, budget});
