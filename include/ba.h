@@ -179,9 +179,10 @@ ba_status ba_check_status(const uint64_t *status_dev, void *stream);
  *                            n0 = 1 or NO_SELF_LOOPS) and for at most 65536 redraws.
  *                            Chains follow the array without rejection, so only the
  *                            node's own output changes.  Needs d <= 1024; combines with
- *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  In a
- *                            degree count every node's targets are recomputed (a second
- *                            chain pass after the count of the array's own targets).
+ *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  A
+ *                            degree count generates the targets chunk by chunk (2^27 edges,
+ *                            2 GB of library scratch from its stream-ordered pool) and
+ *                            counts every edge's final target.
  * The flags combine as stated.  Unknown flags, NO_SELF_LOOPS with n0 < 2, or
  * NO_PARALLEL_EDGES outside its limits give BA_ERR_INVALID_ARG. */
 #define BA_VARIANT_CRC_HASH 1u

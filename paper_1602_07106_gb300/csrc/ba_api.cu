@@ -358,6 +358,9 @@ static ba_status check_variant(uint32_t variant, uint32_t d, uint64_t n0) {
   return BA_OK;
 }
 
+// Edges per chunk of the degree count without parallel edges (16 bytes each of scratch).
+constexpr uint64_t kRejectCountChunk = 1ull << 27;
+
 static_assert(BA_VARIANT_CRC_HASH == kVariantCrc && BA_VARIANT_NO_SELF_LOOPS == kVariantNoLoop,
               "public variant flags and kernel policies disagree");
 
@@ -410,17 +413,41 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
-  Shape shape = shape_for(BA_KIND_DEGREE, edge_end <= (1ull << 31));
-  shape.refill = 1;
-  StreamScratch scratch;
-  st = scratch.alloc(sizeof(unsigned long long), s);
-  if (st != BA_OK) return st;
   const uint32_t draw_flags = variant & (BA_VARIANT_CRC_HASH | BA_VARIANT_NO_SELF_LOOPS);
-  st = launch_degree_variant(g, node_limit, counts_dev, accumulate, shape,
-                             static_cast<unsigned long long *>(scratch.ptr), s, draw_flags);
-  if (st != BA_OK || !(variant & BA_VARIANT_NO_PARALLEL_EDGES)) return st;
-  return launch_count_rejections(g, node_limit, counts_dev, s,
-                                 (variant & BA_VARIANT_NO_SELF_LOOPS) != 0);
+  if (!(variant & BA_VARIANT_NO_PARALLEL_EDGES) || d == 1) {  // d = 1: nothing to reject
+    Shape shape = shape_for(BA_KIND_DEGREE, edge_end <= (1ull << 31));
+    shape.refill = 1;
+    StreamScratch scratch;
+    st = scratch.alloc(sizeof(unsigned long long), s);
+    if (st != BA_OK) return st;
+    return launch_degree_variant(g, node_limit, counts_dev, accumulate, shape,
+                                 static_cast<unsigned long long *>(scratch.ptr), s, draw_flags);
+  }
+  // Without parallel edges: the sources in closed form, then chunk by chunk the array's
+  // targets written by the generate kernel into library scratch and each edge's final
+  // target (after section 4's rejections) counted by the rejection pass -- every chain
+  // runs once, in the refill scheduler.
+  st = launch_degree_sources(g, node_limit, counts_dev, accumulate, s);
+  if (st != BA_OK) return st;
+  const uint64_t a = std::max(edge_begin, g.m0);
+  if (a >= edge_end) return BA_OK;
+  const uint64_t chunk = std::min<uint64_t>(edge_end - a, kRejectCountChunk);
+  StreamScratch pairs, counter;
+  if ((st = pairs.alloc(chunk * 16, s)) != BA_OK) return st;
+  if ((st = counter.alloc(sizeof(unsigned long long), s)) != BA_OK) return st;
+  const Shape gshape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
+  int64_t *buf = static_cast<int64_t *>(pairs.ptr);
+  for (uint64_t c0 = a; c0 < edge_end; c0 += chunk) {
+    const uint64_t c1 = std::min(edge_end, c0 + chunk);
+    const GraphDev gc = make_graph_dev(seed, n, d, n0, c0, c1);
+    if ((st = launch_generate_variant(gc, buf, gshape,
+                                      static_cast<unsigned long long *>(counter.ptr), s,
+                                      draw_flags)) != BA_OK ||
+        (st = launch_count_rejections(gc, buf, node_limit, counts_dev, s,
+                                      (variant & BA_VARIANT_NO_SELF_LOOPS) != 0)) != BA_OK)
+      return st;
+  }
+  return BA_OK;
 }
 
 ba_status ba_generate_edges_host(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,

@@ -83,11 +83,16 @@ ba_status launch_degree_variant(const GraphDev &g, uint64_t node_limit, uint64_t
 // kernel (plain, or self-loop-free with no_loops) has already written; d <= 1024.
 ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
                                    bool no_loops);
-// The same rejections for a degree count: counts[] (below node_limit) already holds the
-// counts of the array's own targets for [g.begin, g.end); each changed edge moves one count
-// from its old target to its new one.  d <= 1024.
-ba_status launch_count_rejections(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
-                                  cudaStream_t stream, bool no_loops);
+// The same rejections for a degree count: `pairs` holds edges [g.begin, g.end) of the
+// array without rejection as the generate kernel wrote them (g.out_edge = 0); counts[]
+// (below node_limit) gets one per edge of the range at its final target.  d <= 1024.
+ba_status launch_count_rejections(const GraphDev &g, const int64_t *pairs, uint64_t node_limit,
+                                  uint64_t *counts, cudaStream_t stream, bool no_loops);
+// counts[j] (j < node_limit) = (accumulate ? counts[j] : 0) + the end points at node j of
+// the edges in [g.begin, g.end) that section 4's graph fixes without a draw: the source of
+// every non-seed edge and both ends of every seed-clique edge (k_degree_init).
+ba_status launch_degree_sources(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                                int accumulate, cudaStream_t stream);
 // launch_generate with every output store checked against out_cap (edges): see SchedParams.
 ba_status launch_generate_checked(const GraphDev &g, int64_t *out, uint64_t out_cap,
                                   unsigned long long *status, const Shape &s,

@@ -865,6 +865,16 @@ ba_status degree_with(const GraphDev &g_in, uint64_t node_limit, uint64_t *count
 
 }  // namespace
 
+ba_status launch_degree_sources(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
+                                int accumulate, cudaStream_t stream) {
+  const int block = 256;
+  const uint64_t want = (node_limit + block - 1) / block;
+  const int grid = static_cast<int>(std::min<uint64_t>(want, static_cast<uint64_t>(sm_count()) * 8));
+  k_degree_init<<<std::max(grid, 1), block, 0, stream>>>(g, g.begin, g.end, node_limit, counts,
+                                                         accumulate);
+  return check_launch("k_degree_init");
+}
+
 ba_status launch_degree(const GraphDev &g, uint64_t node_limit, uint64_t *counts, int accumulate,
                         const Shape &s, unsigned long long *counter, cudaStream_t stream) {
   return degree_with<DrawPlainPtx>(g, node_limit, counts, accumulate, s, counter, stream);

@@ -54,9 +54,10 @@ constexpr uint32_t kNoKey = 0xffffffffu;
 
 // Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]: the W = npw * d edges
 // i0 + item * W + lane (lane < W), i0 = the first edge of node n0 + q_lo; lane = slot*d + j.
-// Count: nothing is stored (section 3's streaming analysis): every target is recomputed by
-// its chain, and a changed edge moves one count from its old target to its new one
-// (counts below node_limit only) instead of being written.
+// Count: `out` is scratch that the generate kernel has just filled with this range's edges
+// (the array's targets, as for the edge list); nothing is written back, and instead every
+// edge's final target below node_limit is counted (section 3's streaming analysis of this
+// graph: the sources are counted in closed form by the caller).
 template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
 __global__ void __launch_bounds__(kThreads)
 k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
@@ -93,7 +94,7 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
       const uint64_t ik = ib + k * W;
       t[k] = 0;
       if (lane < W && ik < g.end) {  // only the range's first node can start before it
-        if (!Count && ik >= g.begin)
+        if (ik >= g.begin)
           t[k] = static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (ik - g.begin))));
         else
           t[k] = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * ik + 1)), g, draw, l2m0);
@@ -120,13 +121,29 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
       }
       flags |= (part && seen) ? 1u << k : 0u;
     }
-    if (__ballot_sync(kAll, flags != 0) == 0) continue;
+    // Count: an edge of the range whose final target is a counted node adds one to it
+    auto count = [&](uint64_t i, uint64_t target) {
+      if constexpr (Count) {
+        if (lane < W && i < g.end && i >= g.begin && target < node_limit)
+          atomicAdd(counts + target, 1ull);
+      }
+    };
+    if (__ballot_sync(kAll, flags != 0) == 0) {
+      if constexpr (Count) {
+#pragma unroll
+        for (int k = 0; k < kGroup; ++k) count(ib + k * W, t[k]);
+      }
+      continue;
+    }
     // Exact pass, node by node, edges in order: an edge whose candidate one of the node's
     // earlier edges has accepted draws again while a new target exists and redraws are left.
 #pragma unroll 1
     for (int k = 0; k < kGroup; ++k) {
       uint32_t dups = __ballot_sync(kAll, (flags >> k) & 1u);
-      if (dups == 0) continue;
+      if (dups == 0) {
+        if constexpr (Count) count(ib + k * W, k == 0 ? t[0] : k == 1 ? t[1] : k == 2 ? t[2] : t[3]);
+        continue;
+      }
       const uint64_t i = ib + k * W;
       const bool part = lane < W && i < g.end;
       const uint32_t parts = __ballot_sync(kAll, part);
@@ -153,13 +170,10 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
         }
         dups &= ~node_lanes;
       }
-      if (part && i >= g.begin && acc != t_k) {
-        if constexpr (Count) {
-          if (t_k < node_limit) atomicAdd(counts + t_k, ~0ull);  // minus one, mod 2^64
-          if (acc < node_limit) atomicAdd(counts + acc, 1ull);
-        } else {
-          __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(acc));
-        }
+      if constexpr (Count) {
+        count(i, acc);
+      } else if (part && i >= g.begin && acc != t_k) {
+        __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(acc));
       }
     }
   }
@@ -220,7 +234,7 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
       if (j < cnt) {
         const uint64_t i = first + j;
         uint64_t t;
-        if (!Count && i >= g.begin)
+        if (i >= g.begin)
           t = static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (i - g.begin))));
         else
           t = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * i + 1)), g, draw, l2m0);
@@ -242,7 +256,20 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
         }
       }
     }
-    if (!__any_sync(kAll, dup)) continue;
+    // Count: every edge of the range adds one to its final target if that is counted
+    auto count_node = [&]() {
+      if constexpr (Count) {
+        __syncwarp();
+        for (uint32_t j = lane; j < cnt; j += 32) {
+          const uint64_t t = tt[j];
+          if (first + j >= g.begin && t < node_limit) atomicAdd(counts + t, 1ull);
+        }
+      }
+    };
+    if (!__any_sync(kAll, dup)) {
+      count_node();
+      continue;
+    }
     __syncwarp();
     const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
     for (uint32_t j = 1; j < cnt; ++j) {
@@ -262,18 +289,13 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
         const uint64_t i = first + j;
         if (lane == 0) {
           tt[j] = cand;
-          if (i >= g.begin) {
-            if constexpr (Count) {
-              if (orig < node_limit) atomicAdd(counts + orig, ~0ull);  // minus one, mod 2^64
-              if (cand < node_limit) atomicAdd(counts + cand, 1ull);
-            } else {
-              __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(cand));
-            }
-          }
+          if (!Count && i >= g.begin)
+            __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(cand));
         }
         __syncwarp();
       }
     }
+    count_node();
   }
 }
 
@@ -358,10 +380,11 @@ ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t
   return reject_range<false>(g, out, nullptr, 0, stream, no_loops);
 }
 
-ba_status launch_count_rejections(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
-                                  cudaStream_t stream, bool no_loops) {
-  return reject_range<true>(g, nullptr, reinterpret_cast<unsigned long long *>(counts), node_limit,
-                            stream, no_loops);
+ba_status launch_count_rejections(const GraphDev &g, const int64_t *pairs, uint64_t node_limit,
+                                  uint64_t *counts, cudaStream_t stream, bool no_loops) {
+  return reject_range<true>(g, const_cast<int64_t *>(pairs),  // read only in this mode
+                            reinterpret_cast<unsigned long long *>(counts), node_limit, stream,
+                            no_loops);
 }
 
 }  // namespace ba

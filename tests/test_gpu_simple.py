@@ -164,7 +164,8 @@ def test_full_size_graph(ba, no_loops, n0):
     assert 0 < changed < m // 1000
 
 
-@pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", CASES)
+@pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", CASES + [(30, 40_000, 1, 0, False, 0, None),
+                                                               (31, 9_000, 1, 2, True, 3, -4)])
 def test_degree_count_bit_exact_against_oracle(ba, seed, n, d, n0, no_loops, a, b):
     m = oracle.num_edges(n, d, n0)
     b = m if b is None else (m + b if b < 0 else b)
