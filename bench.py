@@ -650,6 +650,29 @@ def extras(args, ba, torch, stream, main):
     return ex
 
 
+def mix_plain_rate(ba, torch, stream, shapes, edges_per_call=2**27):
+    """The plain entry point's rate on a mix of graph shapes, on equal terms with a batched
+    or served run of the same mix: one long plain call per shape (d, seed clique or none,
+    32- or 64-bit positions), timed with CUDA events, and the mix's rate = all edges over
+    the sum of each shape's edges at its own rate.  `shapes` maps (d, n0, r64) to the
+    number of edges of that shape in the mix."""
+    buf = torch.empty((edges_per_call, 2), dtype=torch.int64, device="cuda")
+    total_t, total_e, per = 0.0, 0, {}
+    for (d, n0, r64), e in sorted(shapes.items()):
+        n = (2**36 if r64 else 2**31) // d                   # a graph large enough
+        m = ba.ba_num_edges(n, d, n0)
+        a = (m - edges_per_call) if r64 else max(0, min(m, 2**31) - edges_per_call)
+        call = lambda: ba.ba_generate_edges(4242 + d, n, d, n0, a, a + edges_per_call, buf, stream)
+        call()
+        t = statistics.median(_time_events(call, stream, torch, 3))
+        rate = edges_per_call / t
+        per[f"d={d} n0={n0} {'64' if r64 else '32'}-bit"] = rate
+        total_t += e / rate
+        total_e += e
+    del buf
+    return total_e / total_t, per
+
+
 def batched_table(args, ba, torch, stream, plain_rate):
     """All 4096 graphs of the batched table (about 7.3e10 edges, 1.17 TB of pairs) in waves
     of at most --table-wave-edges edges, one persistent launch (a CUDA-graph replay) per
@@ -692,10 +715,20 @@ def batched_table(args, ba, torch, stream, plain_rate):
             off += gg.m
         index += len(w)
     del out_b, scratch
+    torch.cuda.empty_cache()
+    shapes = {}
+    for gg in table:
+        key = (gg.d, 0 if gg.n0 == 0 else gg.d + 1, gg.m > 2**31)
+        shapes[key] = shapes.get(key, 0) + gg.m
+    mix_rate, _ = mix_plain_rate(ba, torch, stream, shapes)
     return {"workload": "the whole 4096-graph table (seed 1000+g, n log-uniform 1e3..1e7, d 1..32, "
                         f"half clique seeds): {edges} edges, {len(waves)} waves of <= {budget} edges",
             "graphs": len(table), "waves": len(waves), "edges": edges, "seconds": secs,
             "edges_per_s": edges / secs, "vs_plain": edges / secs / plain_rate,
+            "plain_same_mix_edges_per_s": mix_rate,
+            "vs_plain_same_mix": edges / secs / mix_rate,
+            "plain_same_mix_how": "one 2^27-edge plain call per (d, seed clique, position "
+                                  "width) shape of the table, weighted by the table's edges",
             "graphs_compared_with_plain_calls": compared, "graphs_equal": equal}
 
 
@@ -742,7 +775,8 @@ def variants(ba, torch, stream, main):
     plain_deg_ms = main["kernels_ms"]["degree"]
     res["no_parallel_edges_degree"] = {
         "workload": f"n=2^27 d=16 n0=0 seed=42 without parallel edges, degree count of nodes "
-                    f"< 1e5 over all {m} edges (the array's count, then every node recomputed)",
+                    f"< 1e5 over all {m} edges (sources in closed form; per 2^27-edge chunk the "
+                    f"generate kernel into scratch and the rejection pass counting final targets)",
         "edges_per_s": m / t, "ms": 1e3 * t, "vs_plain_degree": plain_deg_ms / (1e3 * t)}
     g = W.STREAM_HUGE
     b = g.m // 10
@@ -846,6 +880,12 @@ def serving(args, ba, torch, plain_rate):
     torch.cuda.synchronize()
     plain_same = sat_edges / (time.perf_counter() - t0)
     del scratch, got_buf, want_buf
+    torch.cuda.empty_cache()
+    shapes = {}
+    for r in sat:
+        key = (r.graph.d, 0, r.edge_end > 2**31)
+        shapes[key] = shapes.get(key, 0) + (r.edge_end - r.edge_begin)
+    mix_rate, _ = mix_plain_rate(ba, torch, torch.cuda.current_stream(), shapes)
     lat.sort()
     return {"workload": f"Poisson 2000 req/s for {args.serve_seconds:g} s ({len(trace)} requests; "
                         "n log-uniform 1e4..1e9, d in {2,4,8,16,32}, 1e4..1e8 edges each)",
@@ -861,7 +901,9 @@ def serving(args, ba, torch, plain_rate):
             "saturation_edges_per_s": sat_edges / sat_dt,
             "saturation_vs_plain": (sat_edges / sat_dt) / plain_rate,
             "plain_calls_same_requests_edges_per_s": plain_same,
-            "saturation_vs_plain_same_requests": (sat_edges / sat_dt) / plain_same}
+            "saturation_vs_plain_same_requests": (sat_edges / sat_dt) / plain_same,
+            "plain_same_mix_edges_per_s": mix_rate,
+            "saturation_vs_plain_same_mix": (sat_edges / sat_dt) / mix_rate}
 
 
 def probe_case(args):
