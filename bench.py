@@ -59,7 +59,7 @@ def parse_args():
                     help="edges per wave of the 4096-graph table (16 bytes each on the GPU)")
     ap.add_argument("--cpu-sample-edges", type=int, default=2**28)
     ap.add_argument("--profile", choices=["generate", "degree", "batch", "degree64", "crc",
-                                          "simple"],
+                                          "simple", "simple_wide"],
                     default=None,
                     help="run a small case of one kernel (for ncu captures) and exit")
     ap.add_argument("--profile-edges", type=int, default=2**26)
@@ -102,6 +102,13 @@ def profile_case(args):
         out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
         for _ in range(args.profile_reps):
             ba.ba_generate_edges_variant(g.seed, g.n, g.d, 0, 0, e,
+                                         ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
+    elif args.profile == "simple_wide":
+        # the paper's m = 100n shape without parallel edges: generate + k_reject_duplicates_wide
+        h = W.STREAM_HUGE
+        out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
+        for _ in range(args.profile_reps):
+            ba.ba_generate_edges_variant(h.seed, h.n, h.d, 0, 0, e,
                                          ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
     elif args.profile == "degree":
         # a slice from the middle of the graph: its share of targets below 1e5 (~2%) is
