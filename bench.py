@@ -104,11 +104,12 @@ def profile_case(args):
             ba.ba_generate_edges_variant(g.seed, g.n, g.d, 0, 0, e,
                                          ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
     elif args.profile == "simple_wide":
-        # the paper's m = 100n shape without parallel edges: generate + k_reject_duplicates_wide
+        # the paper's m = 100n shape without parallel edges: generate + k_reject_duplicates_wide,
+        # edges [2^30, 2^30 + e) (past the graph's first nodes, whose many repeats are atypical)
         h = W.STREAM_HUGE
         out = torch.empty((e, 2), dtype=torch.int64, device="cuda")
         for _ in range(args.profile_reps):
-            ba.ba_generate_edges_variant(h.seed, h.n, h.d, 0, 0, e,
+            ba.ba_generate_edges_variant(h.seed, h.n, h.d, 0, 2**30, 2**30 + e,
                                          ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
     elif args.profile == "degree":
         # a slice from the middle of the graph: its share of targets below 1e5 (~2%) is

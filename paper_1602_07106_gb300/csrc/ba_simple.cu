@@ -182,23 +182,30 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
 // ---------------------------------------------------------------- wide nodes, d > 32 --
 //
 // One warp per node: the node's targets (read back, or recomputed for the edges of the
-// range's first node that lie before it, or for every edge when counting) go to the
-// warp's shared row 32 at a time, and each lane inserts the low 32 bits of its target
-// into the warp's open-addressing table (2d..4d slots, linear probing, atomicCAS).  A key
-// that is already there flags the node; a false alarm (equal low halves) only sends the
-// node through the exact pass, which takes the node's edges in order exactly as the
-// narrow kernel does: while an edge's candidate is among the targets accepted before it
-// (a warp-wide scan of the row), j < reach(u) and redraws are left, lane 0 redraws.
+// range's first node that lie before it) go to the warp's shared row 32 at a time, and
+// each lane inserts (low 32 bits of its target, its index) into the warp's open-addressing
+// table (2d..4d slots, linear probing, 64-bit atomicCAS).  A lane that finds its key
+// already there flags both itself and the index stored with it, so every edge whose target
+// repeats another edge's is flagged (a false alarm, equal low halves, only costs work).
+// The exact pass then takes just the flagged edges, in order, as the narrow kernel takes
+// all of them: while the candidate is among the targets accepted before it (a warp-wide
+// scan of the row), j < reach(u) and redraws are left, lane 0 redraws.  A changed target
+// can make a later, unflagged edge collide, so a change flags every later edge holding the
+// new value.  An edge never flagged keeps its target, as the full in-order pass would:
+// nothing accepted before it can equal its target without one of the two flags above.
 constexpr int kWideThreads = 128;
 constexpr uint32_t kWideMaxD = 1024;
+constexpr unsigned long long kNoEntry = ~0ull;
 
 __host__ __device__ constexpr uint32_t wide_table_bits(uint32_t d) {
   uint32_t b = 6;  // at least 64 slots
   while ((1u << b) < 2 * d) ++b;
   return b;
 }
+// Per warp: the row (d targets), the table (8 bytes a slot) and the flags (1 bit an edge).
 __host__ __device__ constexpr size_t wide_warp_bytes(uint32_t d) {
-  return static_cast<size_t>(d) * 8 + (static_cast<size_t>(4) << wide_table_bits(d));
+  return static_cast<size_t>(d) * 8 + (static_cast<size_t>(8) << wide_table_bits(d)) +
+         static_cast<size_t>(kWideMaxD / 32) * 4;
 }
 
 template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
@@ -210,9 +217,13 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
   const uint32_t d = g.d;
   const uint32_t bits = wide_table_bits(d);
   const uint32_t P = 1u << bits;
+  const uint32_t words = (d + 31) / 32;
   unsigned char *mine = wide_smem + static_cast<size_t>(threadIdx.x >> 5) * wide_warp_bytes(d);
-  uint64_t *tt = reinterpret_cast<uint64_t *>(mine);            // the node's targets, d
-  uint32_t *tab = reinterpret_cast<uint32_t *>(mine + static_cast<size_t>(d) * 8);  // P keys
+  uint64_t *tt = reinterpret_cast<uint64_t *>(mine);                      // the node's targets
+  unsigned long long *tab =
+      reinterpret_cast<unsigned long long *>(mine + static_cast<size_t>(d) * 8);  // P entries
+  uint32_t *flag = reinterpret_cast<uint32_t *>(mine + static_cast<size_t>(d) * 8 +
+                                                (static_cast<size_t>(8) << bits));  // words
   Draw draw;
   draw.setup(g, nullptr, sizeof(RT) == 4);
   draw.bind(g);
@@ -220,15 +231,16 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
   const uint32_t lane = threadIdx.x & 31;
   long long *const tgt = reinterpret_cast<long long *>(out) + 1;  // targets: stride 2
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kWideThreads / 32);
+  auto mark = [&](uint32_t j) { atomicOr(flag + (j >> 5), 1u << (j & 31)); };
   for (uint64_t q = q_lo + static_cast<uint64_t>(blockIdx.x) * (kWideThreads / 32) + (threadIdx.x >> 5);
        q <= q_hi; q += warps) {
     const uint64_t node = g.n0 + q;
     const uint64_t first = g.m0 + q * d;
     const uint32_t cnt = static_cast<uint32_t>(min(static_cast<uint64_t>(d), g.end - first));
-    __syncwarp();  // the previous node's row and table are no longer read
-    for (uint32_t k = lane; k < P; k += 32) tab[k] = kNoKey;
+    __syncwarp();  // the previous node's row, table and flags are no longer read
+    for (uint32_t k = lane; k < P; k += 32) tab[k] = kNoEntry;
+    if (lane < words) flag[lane] = 0;
     __syncwarp();
-    bool dup = false;
     for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
       const uint32_t j = j0 + lane;
       if (j < cnt) {
@@ -241,14 +253,16 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
         tt[j] = t;
         const uint32_t key = static_cast<uint32_t>(t);
         if (key == kNoKey) {
-          dup = true;  // the empty marker itself: leave it to the exact pass
+          mark(j);  // the key of an empty slot: every such edge flags itself
         } else {
+          const unsigned long long entry = (static_cast<unsigned long long>(key) << 32) | j;
           uint32_t h = (key * 0x9E3779B1u) >> (32 - bits);
           for (;;) {  // at most d keys in >= 2d slots: an empty slot always exists
-            const uint32_t old = atomicCAS(tab + h, kNoKey, key);
-            if (old == kNoKey) break;
-            if (old == key) {
-              dup = true;
+            const unsigned long long old = atomicCAS(tab + h, kNoEntry, entry);
+            if (old == kNoEntry) break;
+            if (static_cast<uint32_t>(old >> 32) == key) {
+              mark(j);
+              mark(static_cast<uint32_t>(old));
               break;
             }
             h = (h + 1) & (P - 1);
@@ -256,6 +270,7 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
         }
       }
     }
+    __syncwarp();
     // Count: every edge of the range adds one to its final target if that is counted
     auto count_node = [&]() {
       if constexpr (Count) {
@@ -266,33 +281,44 @@ k_reject_duplicates_wide(const GraphDev g, int64_t *__restrict__ out,
         }
       }
     };
-    if (!__any_sync(kAll, dup)) {
+    if (!__any_sync(kAll, lane < words && flag[lane] != 0)) {
       count_node();
       continue;
     }
-    __syncwarp();
     const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
-    for (uint32_t j = 1; j < cnt; ++j) {
-      const uint64_t orig = tt[j];
-      uint64_t cand = orig;
-      uint32_t r = 0;
-      for (;;) {
-        bool taken = false;
-        for (uint32_t l = lane; l < j; l += 32) taken |= tt[l] == cand;
-        if (!__any_sync(kAll, taken) || j >= reach || r >= kRedrawCap) break;
-        ++r;
-        uint64_t v = 0;
-        if (lane == 0) v = redraw<RT, HasSeed>(first + j, r, g, draw, l2m0);
-        cand = __shfl_sync(kAll, v, 0);
-      }
-      if (cand != orig) {
-        const uint64_t i = first + j;
-        if (lane == 0) {
-          tt[j] = cand;
-          if (!Count && i >= g.begin)
-            __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(cand));
+    for (uint32_t w = 0; w < words; ++w) {
+      uint32_t pending = flag[w];
+      while (pending) {
+        const uint32_t b = __ffs(pending) - 1;
+        const uint32_t j = 32 * w + b;
+        if (j > 0 && j < cnt) {  // edge 0 has nothing accepted before it
+          const uint64_t orig = tt[j];
+          uint64_t cand = orig;
+          uint32_t r = 0;
+          for (;;) {
+            bool taken = false;
+            for (uint32_t l = lane; l < j; l += 32) taken |= tt[l] == cand;
+            if (!__any_sync(kAll, taken) || j >= reach || r >= kRedrawCap) break;
+            ++r;
+            uint64_t v = 0;
+            if (lane == 0) v = redraw<RT, HasSeed>(first + j, r, g, draw, l2m0);
+            cand = __shfl_sync(kAll, v, 0);
+          }
+          if (cand != orig) {
+            const uint64_t i = first + j;
+            if (lane == 0) {
+              tt[j] = cand;
+              if (!Count && i >= g.begin)
+                __stcs(tgt + 2 * (g.out_edge + (i - g.begin)), static_cast<long long>(cand));
+            }
+            // a later edge holding the new value now collides with it
+            for (uint32_t k = j + 1 + lane; k < cnt; k += 32)
+              if (tt[k] == cand) mark(k);
+            __syncwarp();
+          }
         }
-        __syncwarp();
+        // the flags above b, read again: the forward scan may have set some
+        pending = flag[w] & ((~0u << b) << 1);
       }
     }
     count_node();
