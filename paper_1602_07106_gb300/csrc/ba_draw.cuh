@@ -20,9 +20,8 @@
 namespace ba {
 
 // Ptx32 / Ptx64: the hash written in PTX on 32-bit / 64-bit positions (hash_r32_pre_ptx,
-// hash_r64_pre_ptx; same values as the C forms).  Measured per kernel: the PTX forms are
-// faster in the degree count on both widths and in generate on 64-bit positions; on
-// 32-bit positions the generate kernel is faster with the compiler's lowering.
+// hash_r64_pre_ptx; same values as the C forms).  The refill kernels (generate, batched,
+// degree count) use the PTX forms on both widths; the rejection passes use the C form.
 template <bool Ptx32, bool Ptx64>
 struct DrawPlainT {
   static constexpr bool kPlain = true;
@@ -40,9 +39,8 @@ struct DrawPlainT {
     else return hash_pre<RT>(spre, r);
   }
 };
-using DrawPlain = DrawPlainT<false, false>;    // the C form everywhere
-using DrawPlainGen = DrawPlainT<false, true>;  // generate and batched kernels
-using DrawPlainPtx = DrawPlainT<true, true>;   // degree count
+using DrawPlain = DrawPlainT<false, false>;   // the C form everywhere
+using DrawPlainPtx = DrawPlainT<true, true>;  // the PTX form everywhere
 
 // CRC-32C in bit-reflected form (polynomial 0x1EDC6F41 reversed).
 constexpr uint32_t kCrc32cReflected = 0x82F63B78u;

@@ -12,16 +12,19 @@
 //                      256-edge chunk of the ring has no chain left in flight, the whole
 //                      warp writes it out: consecutive lanes store consecutive 16-byte
 //                      (source, target) pairs (8-byte int32 pairs for the narrow output).
-//                      The draw is a policy (ba_draw.cuh): h(r), or the variants.
+//                      The draw is a policy (ba_draw.cuh): h(r), or the variants.  The
+//                      fast steps' bookkeeping (stop test, parked store, ballot, hand-out)
+//                      is predicated PTX, so a step has no branch.
 // Degree count (section 3's streaming analysis, no edge stored):
 //   k_degree_init      sources and seed-clique end points in closed form.
 //   k_degree_simple    one thread per edge, global atomics.
 //   k_degree_refill    the refill scheduler of k_generate_refill; chains that stop below
-//                      the position of the first uncounted node are parked in a per-warp
-//                      ring and counted 32 at a time: targets below the shared-memory
-//                      limit in a per-CTA 64-bit histogram (optionally one atomic per
-//                      distinct node per warp, __match_any_sync), the rest with global
-//                      64-bit atomics.
+//                      the position of the first uncounted node are parked in per-lane
+//                      hit buffers (one predicated store) and counted by the whole warp
+//                      when a buffer is half full: targets below the shared-memory limit
+//                      in a per-CTA 64-bit histogram (optionally one atomic per distinct
+//                      node per warp, __match_any_sync), the rest with global 64-bit
+//                      atomics.
 #include <algorithm>
 #include <type_traits>
 
@@ -97,13 +100,23 @@ __device__ __forceinline__ void copy_graph(GraphDev *dst, const GraphDev *src) {
 // with Narrow int32 pairs).
 // Checked: a store to slot out_cap or beyond is skipped and the lowest such slot is kept in
 // *status (the checked launch; the slot bound comes from the caller, not from the range).
-template <class RT, bool HasSeed, bool Narrow = false, bool Checked = false>
+template <class RT, bool HasSeed, bool Narrow = false, bool Checked = false, bool Full = false>
 __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint32_t len,
                                            const GraphDev &g, int64_t *__restrict__ out,
                                            uint64_t out_cap = 0,
                                            unsigned long long *status = nullptr) {
   __syncwarp();
   const uint64_t out0 = g.out_edge + (base - g.begin);
+  // fn(j, k) for the lane's edges j = lane + 32k < len; Full: len is 256 (8 per lane)
+  auto each = [&](auto fn) {
+    if constexpr (Full) {
+#pragma unroll
+      for (uint32_t k = 0; k < 8; ++k) fn((threadIdx.x & 31) + 32 * k, k);
+    } else {
+      uint32_t k = 0;
+      for (uint32_t j = threadIdx.x & 31; j < len; j += 32, ++k) fn(j, k);
+    }
+  };
   // false (and the slot recorded) when slot k does not exist
   [[maybe_unused]] auto slot_ok = [&](uint64_t k) {
     if constexpr (Checked) {
@@ -145,25 +158,22 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
       if (n0 == 0) {  // also the unseeded graphs of a batched launch that has seeded ones
         // Empty seed graph: source i/d, target (r/2)/d; with d = 2^l both are one shift.
         const uint32_t l1 = dv.l + 1;
-#pragma unroll 8
-        for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+        each([&](uint32_t j, uint32_t) {
           const uint32_t r = stage[j];
           if constexpr (Pow2) put(j, (b32 + j) >> dv.l, r >> l1);
           else put(j, div(b32 + j), div(r >> 1));
-        }
+        });
       } else {
         // A chain that stopped inside the seed names a clique node (a few in 10^4 chains:
         // the seed nodes' share of all end points).  Bit k of `fix` marks the lane's k-th
         // edge of the chunk as one; those few pairs are rewritten afterwards.
         [[maybe_unused]] uint32_t fix = 0;
-        uint32_t bit = 1;
-#pragma unroll 4
-        for (uint32_t j = threadIdx.x & 31; j < len; j += 32, bit <<= 1) {
+        each([&](uint32_t j, uint32_t k) {
           const uint32_t i = b32 + j;
           const uint32_t r = stage[j];
-          if constexpr (HasSeed) fix |= r < two_m0 ? bit : 0u;
+          if constexpr (HasSeed) fix |= r < two_m0 ? 1u << k : 0u;
           put(j, n0 + div(i - m0), n0 + div((r >> 1) - m0));
-        }
+        });
         if constexpr (HasSeed) {
           if (__any_sync(kFull, fix != 0)) {
             while (fix) {  // by the lane that wrote the pair
@@ -192,12 +202,12 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
     // Empty seed graph, d = 2^l (every request of a typical serving mix): one shift each
     // instead of two 64-bit multiply-highs.
     const uint32_t l = g.div.l;
-#pragma unroll 4
-    for (uint32_t j = threadIdx.x & 31; j < len; j += 32)
+    each([&](uint32_t j, uint32_t) {
       if (slot_ok(out0 + j))
         store_pair<Narrow>(out, out0 + j, (base + j) >> l, static_cast<uint64_t>(stage[j]) >> (l + 1));
+    });
   } else {
-    for (uint32_t j = threadIdx.x & 31; j < len; j += 32) {
+    each([&](uint32_t j, uint32_t) {
       const uint64_t i = base + j;
       uint64_t u, v;
       if (HasSeed && i < g.m0) {
@@ -208,7 +218,7 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
         v = target_of<RT, HasSeed>(stage[j], g);
       }
       if (slot_ok(out0 + j)) store_pair<Narrow>(out, out0 + j, u, v);
-    }
+    });
   }
   __syncwarp();
 }
@@ -220,10 +230,119 @@ __device__ __forceinline__ void flush_tile(const RT *stage, uint64_t base, uint3
 constexpr uint32_t kRing = 1024;
 constexpr uint32_t kChunk = 256;
 
+// One fast step's bookkeeping for one chain as predicated PTX: the stop test of Fig. 1
+// (r even, or inside the seed clique), the parked store of a final r into the staging ring,
+// the warp's ballot and the hand-out of the next IDs of the tile (rank among the stopped
+// lanes).  r, o and hoff are updated in place; ring_s is the ring's shared-space address.
+template <bool Seed>
+__device__ __forceinline__ void park_and_refill(uint32_t &r, uint32_t &o, uint32_t &hoff,
+                                                uint32_t lt, uint32_t r0, uint32_t two_m0,
+                                                uint32_t ring_s) {
+  if constexpr (Seed) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .u32 t, a, fm, x;\n\t"
+        "and.b32 t, %0, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.or.u32 p, %0, %6, p;\n\t"
+        "and.b32 a, %1, 1023;\n\t"
+        "shl.b32 a, a, 2;\n\t"
+        "add.u32 a, a, %5;\n\t"
+        "@p st.shared.u32 [a], %0;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "@p add.u32 %1, %2, x;\n\t"
+        "@p mad.lo.u32 %0, %1, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %2, %2, x;\n\t"
+        "}"
+        : "+r"(r), "+r"(o), "+r"(hoff)
+        : "r"(lt), "r"(r0), "r"(ring_s), "r"(two_m0)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .u32 t, a, fm, x;\n\t"
+        "and.b32 t, %0, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "and.b32 a, %1, 1023;\n\t"
+        "shl.b32 a, a, 2;\n\t"
+        "add.u32 a, a, %5;\n\t"
+        "@p st.shared.u32 [a], %0;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "@p add.u32 %1, %2, x;\n\t"
+        "@p mad.lo.u32 %0, %1, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %2, %2, x;\n\t"
+        "}"
+        : "+r"(r), "+r"(o), "+r"(hoff)
+        : "r"(lt), "r"(r0), "r"(ring_s)
+        : "memory");
+  }
+}
+template <bool Seed>
+__device__ __forceinline__ void park_and_refill(uint64_t &r, uint32_t &o, uint32_t &hoff,
+                                                uint32_t lt, uint64_t r0, uint64_t two_m0,
+                                                uint32_t ring_s) {
+  if constexpr (Seed) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .u32 t, a, fm, x;\n\t"
+        "cvt.u32.u64 t, %0;\n\t"
+        "and.b32 t, t, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.or.u64 p, %0, %6, p;\n\t"
+        "and.b32 a, %1, 1023;\n\t"
+        "shl.b32 a, a, 3;\n\t"
+        "add.u32 a, a, %5;\n\t"
+        "@p st.shared.u64 [a], %0;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "@p add.u32 %1, %2, x;\n\t"
+        "@p mad.wide.u32 %0, %1, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %2, %2, x;\n\t"
+        "}"
+        : "+l"(r), "+r"(o), "+r"(hoff)
+        : "r"(lt), "l"(r0), "r"(ring_s), "l"(two_m0)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .u32 t, a, fm, x;\n\t"
+        "cvt.u32.u64 t, %0;\n\t"
+        "and.b32 t, t, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "and.b32 a, %1, 1023;\n\t"
+        "shl.b32 a, a, 3;\n\t"
+        "add.u32 a, a, %5;\n\t"
+        "@p st.shared.u64 [a], %0;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "@p add.u32 %1, %2, x;\n\t"
+        "@p mad.wide.u32 %0, %1, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %2, %2, x;\n\t"
+        "}"
+        : "+l"(r), "+r"(o), "+r"(hoff)
+        : "r"(lt), "l"(r0), "r"(ring_s)
+        : "memory");
+  }
+}
+
 // K chains per lane: lane l runs the chains of virtual lanes l, l+32, ..., l+32(K-1), so
 // each lane has K independent hash chains in flight.  The hash is one long dependency
 // chain of integer multiplies and shifts; a second chain per lane hides its latency.
-template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlain,
+template <class RT, bool HasSeed, bool Batched, bool Narrow = false, class Draw = DrawPlainPtx,
           int K = 1, bool Checked = false>
 __global__ void __launch_bounds__(1024)
 k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
@@ -235,6 +354,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   const int wib = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
   RT *ring = reinterpret_cast<RT *>(smem_raw) + static_cast<size_t>(wib) * kRing;
+  const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
   GraphDev *sg = nullptr;
   if constexpr (Batched)
     sg = reinterpret_cast<GraphDev *>(smem_raw + static_cast<size_t>(warps) * kRing * sizeof(RT)) + wib;
@@ -244,6 +364,7 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * warps + wib;
   constexpr uint32_t kLanes = 32u * K;  // virtual lanes of the warp
+  constexpr uint32_t kSteps = 2;  // fast steps per loop iteration
   bool first = true;
 
   for (;;) {  // one tile of up to T edges at a time (section 2: batches of edge IDs)
@@ -266,6 +387,10 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
       flush_tile<RT, HasSeed, Narrow, Checked>(ring + (from & (kRing - 1)), base + from, count, g,
                                                out, sp.out_cap, sp.status);
     };
+    auto flush_full = [&](uint32_t from) {  // a whole chunk: a fixed trip count per lane
+      flush_tile<RT, HasSeed, Narrow, Checked, true>(ring + (from & (kRing - 1)), base + from,
+                                                     kChunk, g, out, sp.out_cap, sp.status);
+    };
 
     // Chain c of this lane: edge base+o[c] at position r[c] while busy[c].
     uint32_t hoff = min(kLanes, len);
@@ -281,30 +406,19 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     uint32_t flushed = 0;  // edges [0, flushed) of the tile are written out
     bool all_busy = hoff == kLanes;
 
-    // Fast steps: every chain busy and >= 64K IDs may still be handed out before the ring
-    // is full or the tile ends; a chain that stops parks r and starts the next ID.
+    // Fast steps: every chain busy and >= kSteps*kLanes IDs may still be handed out before
+    // the ring is full or the tile ends; a chain that stops parks r and starts the next ID.
+    // The bookkeeping is predicated PTX (park_and_refill): no branch per step.
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
-      const uint32_t last = min(len, flushed + kRing) - 2 * kLanes;
+      const uint32_t last = min(len, flushed + kRing) - kSteps * kLanes;
       do {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          bool stop[K];
+        for (uint32_t u = 0; u < kSteps; ++u) {
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-            r[c] = draw(r[c]);
-            stop[c] = chain_stops<RT, Seed>(r[c], l2m0);
-          }
+          for (int c = 0; c < K; ++c) r[c] = draw(r[c]);
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-            if (stop[c]) ring[o[c] & (kRing - 1)] = r[c];
-            const uint32_t fm = __ballot_sync(kFull, stop[c]);
-            if (stop[c]) {
-              o[c] = hoff + __popc(fm & lt);
-              r[c] = r0 + 2 * static_cast<RT>(o[c]);
-            }
-            hoff += __popc(fm);
-          }
+          for (int c = 0; c < K; ++c) park_and_refill<Seed>(r[c], o[c], hoff, lt, r0, l2m0, ring_s);
         }
       } while (hoff <= last);
     };
@@ -316,19 +430,19 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     };
 
     for (;;) {
-      if (all_busy && hoff + 2 * kLanes <= min(len, flushed + kRing)) {
+      if (all_busy && hoff + kSteps * kLanes <= min(len, flushed + kRing)) {
         if (HasSeed && l2m0 != 0) fast_loop(std::true_type{});
         else fast_loop(std::false_type{});
       }
       // Make room: write out the oldest chunks whose edges are all done.
       bool made_room = false;
       while (flushed + kChunk <= hoff && !in_flight_below(flushed + kChunk)) {
-        flush(flushed, kChunk);
+        flush_full(flushed);
         flushed += kChunk;
         made_room = true;
       }
       // Every chain still busy and room again: back to the fast steps directly.
-      if (made_room && all_busy && hoff + 2 * kLanes <= min(len, flushed + kRing)) continue;
+      if (made_room && all_busy && hoff + kSteps * kLanes <= min(len, flushed + kRing)) continue;
       if (hoff == len && !in_flight_below(len)) break;  // tile done
       // General step: some chains idle, or the ring or the tile is nearly used up.
       uint32_t room = min(len, flushed + kRing) - hoff;
@@ -442,7 +556,8 @@ __device__ __forceinline__ void histogram_add(bool hit, uint64_t v, unsigned lon
     atomicAdd(bins + v, static_cast<unsigned long long>(__popc(peers)));
 }
 
-// Entries of the per-warp ring of stopped positions that may hit a counted node.
+// Entries per warp of the hit buffers (stopped positions that may hit a counted node):
+// 16 slots per lane.
 constexpr uint32_t kHitRing = 512;
 
 // One end point at node v from the calling lane alone: a shared-memory bin below `hot`,
@@ -453,6 +568,131 @@ __device__ __forceinline__ void histogram_add_lane(uint64_t v, unsigned long lon
   else atomicAdd(reinterpret_cast<unsigned long long *>(counts + v), 1ull);
 }
 
+// One fast step of the degree count for one chain as predicated PTX: the stop test, a
+// stopped position below hp parked in the lane's own hit buffer (slot address hptr, the
+// next slot 32 entries further), the warp's ballot and the hand-out of the next IDs.
+template <bool Seed>
+__device__ __forceinline__ void count_step(uint32_t &r, uint32_t &hoff, uint32_t &hptr,
+                                           uint32_t lt, uint32_t r0, uint32_t two_m0,
+                                           uint32_t hp) {
+  if constexpr (Seed) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h;\n\t"
+        ".reg .u32 t, fm, x;\n\t"
+        "and.b32 t, %0, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.or.u32 p, %0, %5, p;\n\t"
+        "setp.lt.and.u32 h, %0, %6, p;\n\t"
+        "@h st.shared.u32 [%2], %0;\n\t"
+        "@h add.u32 %2, %2, 128;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "add.u32 x, %1, x;\n\t"
+        "@p mad.lo.u32 %0, x, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %1, %1, x;\n\t"
+        "}"
+        : "+r"(r), "+r"(hoff), "+r"(hptr)
+        : "r"(lt), "r"(r0), "r"(two_m0), "r"(hp)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h;\n\t"
+        ".reg .u32 t, fm, x;\n\t"
+        "and.b32 t, %0, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.and.u32 h, %0, %5, p;\n\t"
+        "@h st.shared.u32 [%2], %0;\n\t"
+        "@h add.u32 %2, %2, 128;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "add.u32 x, %1, x;\n\t"
+        "@p mad.lo.u32 %0, x, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %1, %1, x;\n\t"
+        "}"
+        : "+r"(r), "+r"(hoff), "+r"(hptr)
+        : "r"(lt), "r"(r0), "r"(hp)
+        : "memory");
+  }
+}
+template <bool Seed>
+__device__ __forceinline__ void count_step(uint64_t &r, uint32_t &hoff, uint32_t &hptr,
+                                           uint32_t lt, uint64_t r0, uint64_t two_m0,
+                                           uint64_t hp) {
+  if constexpr (Seed) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h;\n\t"
+        ".reg .u32 t, fm, x;\n\t"
+        "cvt.u32.u64 t, %0;\n\t"
+        "and.b32 t, t, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.or.u64 p, %0, %5, p;\n\t"
+        "setp.lt.and.u64 h, %0, %6, p;\n\t"
+        "@h st.shared.u64 [%2], %0;\n\t"
+        "@h add.u32 %2, %2, 256;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "add.u32 x, %1, x;\n\t"
+        "@p mad.wide.u32 %0, x, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %1, %1, x;\n\t"
+        "}"
+        : "+l"(r), "+r"(hoff), "+r"(hptr)
+        : "r"(lt), "l"(r0), "l"(two_m0), "l"(hp)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, h;\n\t"
+        ".reg .u32 t, fm, x;\n\t"
+        "cvt.u32.u64 t, %0;\n\t"
+        "and.b32 t, t, 1;\n\t"
+        "setp.eq.u32 p, t, 0;\n\t"
+        "setp.lt.and.u64 h, %0, %5, p;\n\t"
+        "@h st.shared.u64 [%2], %0;\n\t"
+        "@h add.u32 %2, %2, 256;\n\t"
+        "vote.sync.ballot.b32 fm, p, 0xffffffff;\n\t"
+        "and.b32 x, fm, %3;\n\t"
+        "popc.b32 x, x;\n\t"
+        "add.u32 x, %1, x;\n\t"
+        "@p mad.wide.u32 %0, x, 2, %4;\n\t"
+        "popc.b32 x, fm;\n\t"
+        "add.u32 %1, %1, x;\n\t"
+        "}"
+        : "+l"(r), "+r"(hoff), "+r"(hptr)
+        : "r"(lt), "l"(r0), "l"(hp)
+        : "memory");
+  }
+}
+
+// A parked position in the per-lane hit buffers, by shared-space address (the buffers are
+// written by the PTX steps, so they are read and written through PTX too).
+__device__ __forceinline__ void st_shared_pos(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared_pos(uint32_t a, uint64_t v) {
+  asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+template <class RT>
+__device__ __forceinline__ RT ld_shared_pos(uint32_t a) {
+  if constexpr (sizeof(RT) == 4) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+  } else {
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+  }
+}
+
 // K chains per lane, as in k_generate_refill.
 template <class RT, bool HasSeed, class Draw = DrawPlain, int K = 1>
 __global__ void __launch_bounds__(1024, 1)
@@ -461,7 +701,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   extern __shared__ __align__(16) unsigned long long bins[];
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) bins[b] = 0;
   __syncthreads();
-  Draw draw;  // tables (if any) after the bins and the hit rings
+  Draw draw;  // tables (if any) after the bins and the hit buffers
   draw.setup(g, reinterpret_cast<uint32_t *>(reinterpret_cast<RT *>(bins + hot) +
                                              static_cast<size_t>(blockDim.x >> 5) * kHitRing),
              sizeof(RT) == 4);
@@ -473,10 +713,9 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kLanes = 32u * K;
-  // Fast steps between bounds checks and ring drains: 4 on the 32-bit path; the 64-bit
+  // Fast steps between bounds checks and hit drains: 4 on the 32-bit path; the 64-bit
   // path's longer hash runs out of registers with 4 (measured slower) and takes 2.
   constexpr uint32_t kSteps = sizeof(RT) == 4 ? 4 : 2;
-  static_assert(31 + kSteps * kLanes <= kHitRing, "a fast iteration's hits must fit in the hit ring");
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
   const bool agg = sp.hist_agg != 0;
@@ -485,38 +724,34 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const RT hp = (sizeof(RT) == 4 && hit_pos > 0xffffffffull) ? static_cast<RT>(0xffffffffu)
                                                              : static_cast<RT>(hit_pos);
 
-  // Stopped positions below hp wait in a per-warp ring of kHitRing; once 32 have gathered
-  // the whole warp resolves them together (one target per lane) and counts them.  The ring
-  // is drained below 32 after every general-step push and after every two fast steps.
-  RT *ring = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * kHitRing;
-  uint32_t qhead = 0, qtail = 0;  // warp-uniform
-  auto drain = [&](uint32_t k) {  // ring entries qhead .. qhead+k-1, k <= 32
-    __syncwarp();
-    bool hit = static_cast<uint32_t>(lane) < k;
-    uint64_t v = 0;
-    if (hit) {
-      v = target_of<RT, HasSeed>(ring[(qhead + lane) & (kHitRing - 1)], g);
-      hit = v < node_limit;
+  // Stopped positions below hp are parked in the lane's own hit buffer: kLaneHits slots,
+  // slot k of lane l at entry k*32 + l of the warp's kHitRing entries, hptr the lane's next
+  // free slot.  Parking is one predicated store, with no ballot.  A fast iteration adds at
+  // most kSteps*K per lane and a general step at most K, and after each of them the warp
+  // resolves and counts every parked position once any lane holds more than half its slots.
+  constexpr uint32_t kLaneHits = kHitRing / 32;
+  constexpr uint32_t kSlot = 32u * sizeof(RT);  // bytes from one slot of a lane to the next
+  static_assert(kSteps * K <= kLaneHits / 2, "a fast iteration's hits must fit in a lane's buffer");
+  RT *hits = reinterpret_cast<RT *>(bins + hot) + static_cast<size_t>(threadIdx.x >> 5) * kHitRing;
+  const uint32_t hbuf_s = static_cast<uint32_t>(__cvta_generic_to_shared(hits + lane));
+  uint32_t hptr = hbuf_s;
+  auto drain = [&]() {  // warp-collective: every parked position of every lane
+    uint32_t n = (hptr - hbuf_s) / kSlot;
+    while (__any_sync(kFull, n != 0)) {
+      bool hit = n != 0;
+      uint64_t v = 0;
+      if (hit) {
+        --n;
+        v = target_of<RT, HasSeed>(ld_shared_pos<RT>(hbuf_s + n * kSlot), g);
+        hit = v < node_limit;
+      }
+      if (agg) histogram_add(hit, v, bins, hot, counts);
+      else if (hit) histogram_add_lane(v, bins, hot, counts);
     }
-    if (agg) histogram_add(hit, v, bins, hot, counts);
-    else if (hit) histogram_add_lane(v, bins, hot, counts);
-    qhead += k;
-    __syncwarp();
+    hptr = hbuf_s;
   };
-  auto push = [&](bool hit, RT rv) {  // warp-collective
-    const uint32_t hm = __ballot_sync(kFull, hit);
-    if (hm) {  // most steps have no hit at all
-      if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = rv;
-      qtail += __popc(hm);
-      if (qtail - qhead >= 32) drain(32);
-    }
-  };
-  // The fast steps' form: no branch per step (the pushes are predicated stores), the ring
-  // is drained after every two steps, which add at most 64K entries to < 32 waiting.
-  auto push_nobranch = [&](bool hit, RT rv) {  // warp-collective
-    const uint32_t hm = __ballot_sync(kFull, hit);
-    if (hit) ring[(qtail + __popc(hm & lt)) & (kHitRing - 1)] = rv;
-    qtail += __popc(hm);
+  auto maybe_drain = [&]() {
+    if (__any_sync(kFull, hptr - hbuf_s > (kLaneHits / 2) * kSlot)) drain();
   };
 
   for (;;) {  // one tile at a time
@@ -536,31 +771,20 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
     }
     bool all_busy = hoff == kLanes;
 
-    // Fast steps: every chain busy and >= 64K IDs left.
+    // Fast steps: every chain busy and >= kSteps*kLanes IDs left; the bookkeeping is
+    // predicated PTX (count_step): no branch per step.
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
       const uint32_t last = len - kSteps * kLanes;
       do {
 #pragma unroll
-        for (int u = 0; u < kSteps; ++u) {
-          bool stop[K];
+        for (uint32_t u = 0; u < kSteps; ++u) {
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-            r[c] = draw(r[c]);
-            stop[c] = chain_stops<RT, Seed>(r[c], two_m0);
-          }
+          for (int c = 0; c < K; ++c) r[c] = draw(r[c]);
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-            // 32-bit path: predicated pushes; 64-bit path: one uniform branch (measured
-            // faster there)
-            if constexpr (sizeof(RT) == 4) push_nobranch(stop[c] && r[c] < hp, r[c]);
-            else push(stop[c] && r[c] < hp, r[c]);
-            const uint32_t fm = __ballot_sync(kFull, stop[c]);
-            if (stop[c]) r[c] = r0 + 2 * static_cast<RT>(hoff + __popc(fm & lt));
-            hoff += __popc(fm);
-          }
+          for (int c = 0; c < K; ++c) count_step<Seed>(r[c], hoff, hptr, lt, r0, two_m0, hp);
         }
-        while (qtail - qhead >= 32) drain(32);
+        maybe_drain();
       } while (hoff <= last);
     };
 
@@ -573,7 +797,7 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
 #pragma unroll
       for (int c = 0; c < K; ++c) any_busy |= busy[c];
       if (hoff == len && !__any_sync(kFull, any_busy)) break;  // tile done
-      // General step: some chains idle, or fewer than 64K IDs left.
+      // General step: some chains idle, or fewer than kSteps*kLanes IDs left.
       bool idle = false;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -582,7 +806,10 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
           r[c] = draw(r[c]);
           stop = chain_stops<RT, HasSeed>(r[c], two_m0);
         }
-        push(stop && r[c] < hp, r[c]);
+        if (stop && r[c] < hp) {
+          st_shared_pos(hptr, r[c]);
+          hptr += kSlot;
+        }
         if (stop) busy[c] = false;
         const uint32_t fm = __ballot_sync(kFull, !busy[c]);
         const uint32_t k = min(len - hoff, static_cast<uint32_t>(__popc(fm)));
@@ -595,9 +822,10 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
         idle |= !busy[c];
       }
       all_busy = __ballot_sync(kFull, idle) == 0;
+      maybe_drain();
     }
   }
-  while (qtail != qhead) drain(min(32u, qtail - qhead));
+  drain();
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < hot; b += blockDim.x) {
     const unsigned long long c = bins[b];
@@ -645,7 +873,7 @@ ba_status check_launch(const char *what) {
   return e == cudaSuccess ? BA_OK : cuda_fail(e, what);
 }
 
-template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlainGen, bool Checked = false>
+template <class RT, bool HasSeed, bool Narrow, class Draw = DrawPlainPtx, bool Checked = false>
 ba_status generate_t(const GraphDev &g, int64_t *out, const Shape &s, unsigned long long *counter,
                      cudaStream_t stream, uint64_t out_cap = 0,
                      unsigned long long *status = nullptr) {
@@ -711,7 +939,7 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
   const int warps = block / 32;
   const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
   const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
-                      static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit rings
+                      static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit buffers
                       (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
   auto kernel = s.chains == 2 ? k_degree_refill<RT, HasSeed, Draw, 2>
                               : k_degree_refill<RT, HasSeed, Draw, 1>;
@@ -744,8 +972,8 @@ ba_status batch_t(const BatchTable &tab, uint64_t total_tiles, int64_t *out, con
   const int warps = block / 32;
   const size_t smem = static_cast<size_t>(warps) * kRing * sizeof(RT) +
                       static_cast<size_t>(warps) * sizeof(GraphDev);
-  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, true, false, DrawPlainGen, 2>
-                              : k_generate_refill<RT, HasSeed, true, false, DrawPlainGen, 1>;
+  auto kernel = s.chains == 2 ? k_generate_refill<RT, HasSeed, true, false, DrawPlainPtx, 2>
+                              : k_generate_refill<RT, HasSeed, true, false, DrawPlainPtx, 1>;
   ba_status st = set_smem(kernel, smem);
   if (st != BA_OK) return st;
   SchedParams sp{};
@@ -794,10 +1022,10 @@ ba_status launch_generate_checked(const GraphDev &g, int64_t *out, uint64_t out_
   s.refill = 1;  // the checks live in the refill kernel's store path
   const bool r32 = g.end <= (1ull << 31);
   if (g.m0 > 0)
-    return r32 ? generate_t<uint32_t, true, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status)
-               : generate_t<uint64_t, true, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status);
-  return r32 ? generate_t<uint32_t, false, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status)
-             : generate_t<uint64_t, false, false, DrawPlainGen, true>(g, out, s, counter, stream, out_cap, status);
+    return r32 ? generate_t<uint32_t, true, false, DrawPlainPtx, true>(g, out, s, counter, stream, out_cap, status)
+               : generate_t<uint64_t, true, false, DrawPlainPtx, true>(g, out, s, counter, stream, out_cap, status);
+  return r32 ? generate_t<uint32_t, false, false, DrawPlainPtx, true>(g, out, s, counter, stream, out_cap, status)
+             : generate_t<uint64_t, false, false, DrawPlainPtx, true>(g, out, s, counter, stream, out_cap, status);
 }
 
 namespace {

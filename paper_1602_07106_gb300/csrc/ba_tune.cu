@@ -40,7 +40,7 @@ Shape default_shape(int kind) {
       s.chains = 2;
       break;
     default:  // generate and batch
-      s.block = 256; s.ctas_per_sm = 4; s.tile = 16384; s.refill = 1; s.hist_bins = 0;
+      s.block = 256; s.ctas_per_sm = 4; s.tile = 65536; s.refill = 1; s.hist_bins = 0;
       s.chains = 2;
       break;
   }
