@@ -409,10 +409,16 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
     // Fast steps: every chain busy and >= kSteps*kLanes IDs may still be handed out before
     // the ring is full or the tile ends; a chain that stops parks r and starts the next ID.
     // The bookkeeping is predicated PTX (park_and_refill): no branch per step.
+    auto in_flight_below = [&](uint32_t edge) {  // any chain of the warp on an edge < edge?
+      bool any = false;
+#pragma unroll
+      for (int c = 0; c < K; ++c) any |= busy[c] && o[c] < edge;
+      return __any_sync(kFull, any);
+    };
     auto fast_loop = [&](auto seed_tag) {
       constexpr bool Seed = decltype(seed_tag)::value;
-      const uint32_t last = min(len, flushed + kRing) - kSteps * kLanes;
-      do {
+      uint32_t last = min(len, flushed + kRing) - kSteps * kLanes;
+      for (;;) {
 #pragma unroll
         for (uint32_t u = 0; u < kSteps; ++u) {
 #pragma unroll
@@ -420,13 +426,15 @@ k_generate_refill(const GraphDev g0, const BatchTable tab, const SchedParams sp,
 #pragma unroll
           for (int c = 0; c < K; ++c) park_and_refill<Seed>(r[c], o[c], hoff, lt, r0, l2m0, ring_s);
         }
-      } while (hoff <= last);
-    };
-    auto in_flight_below = [&](uint32_t edge) {  // any chain of the warp on an edge < edge?
-      bool any = false;
-#pragma unroll
-      for (int c = 0; c < K; ++c) any |= busy[c] && o[c] < edge;
-      return __any_sync(kFull, any);
+        if (hoff <= last) continue;
+        // The ring is nearly full (or the tile nearly used up): write the oldest chunk out
+        // without leaving the fast steps when the ring is the limit and the chunk is done.
+        if (flushed + kRing >= len || in_flight_below(flushed + kChunk)) break;
+        flush_full(flushed);
+        flushed += kChunk;
+        last = min(len, flushed + kRing) - kSteps * kLanes;
+        if (hoff > last) break;
+      }
     };
 
     for (;;) {
@@ -713,9 +721,8 @@ k_degree_refill(const GraphDev g, const SchedParams sp, uint64_t hit_pos, uint64
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   constexpr uint32_t kLanes = 32u * K;
-  // Fast steps between bounds checks and hit drains: 4 on the 32-bit path; the 64-bit
-  // path's longer hash runs out of registers with 4 (measured slower) and takes 2.
-  constexpr uint32_t kSteps = sizeof(RT) == 4 ? 4 : 2;
+  // Fast steps between bounds checks and hit drains.
+  constexpr uint32_t kSteps = 4;
   bool first = true;
   const RT two_m0 = seed_limit<RT>(g.two_m0);
   const bool agg = sp.hist_agg != 0;
