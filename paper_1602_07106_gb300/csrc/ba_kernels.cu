@@ -944,10 +944,14 @@ ba_status degree_t(const GraphDev &g, uint64_t hit_pos, uint64_t node_limit, uin
     }
   }
   const int warps = block / 32;
-  const uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
-  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) +
-                      static_cast<size_t>(warps) * kHitRing * sizeof(RT) +  // bins + hit buffers
-                      (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
+  // The shape's shared-memory bins, fewer when the hit buffers and the draw's tables leave
+  // less room (a shape tuned for the plain draw also serves the table-driven ones).
+  const size_t fixed = static_cast<size_t>(warps) * kHitRing * sizeof(RT) +
+                       (Draw::kTables ? crc_table_smem(sizeof(RT) == 4) : 0);
+  uint32_t hot = static_cast<uint32_t>(std::min<uint64_t>(node_limit, std::max(s.hist_bins, 0)));
+  if (fixed < kMaxSmemPerCta)
+    hot = static_cast<uint32_t>(std::min<size_t>(hot, (kMaxSmemPerCta - fixed) / sizeof(unsigned long long)));
+  const size_t smem = static_cast<size_t>(hot) * sizeof(unsigned long long) + fixed;
   auto kernel = s.chains == 2 ? k_degree_refill<RT, HasSeed, Draw, 2>
                               : k_degree_refill<RT, HasSeed, Draw, 1>;
   ba_status st = set_smem(kernel, smem);

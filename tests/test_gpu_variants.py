@@ -142,3 +142,21 @@ def test_crc_degree_count_of_the_paper_experiment_shape(ba):
     want = opar.degree_count_range_variant(seed, n, d, 0, oracle.HASH_CRC, False, 0, b, limit)
     np.testing.assert_array_equal(got, want)
     assert int(got.sum()) == 2 * b
+
+
+def test_degree_shape_with_full_shared_bins_still_runs_the_table_draws(ba):
+    # A degree shape whose bins fill the shared memory with the plain draw (the 64-bit
+    # path's hit buffers at 1024 threads, 24576 bins): the table-driven hash_crc count gets
+    # fewer bins, not an error, and the same counts.
+    seed, n, d, n0, limit = 44, 10**10, 100, 101, 100_000
+    m = ba.ba_num_edges(n, d, n0)
+    a, b = m - 1_000_000, m                                    # 64-bit positions
+    want = opar.degree_count_range_variant(seed, n, d, n0, oracle.HASH_CRC, True, a, b, limit)
+    big = {"refill": 1, "block": 1024, "ctas_per_sm": 1, "tile": 65536, "hist_bins": 24576,
+           "chains": 2}
+    try:
+        ba.ba_set_tuning(ba.BA_KIND_DEGREE, big)
+        got = _deg_gpu(ba, seed, n, d, n0, a, b, limit, CRC | NOLOOP)
+    finally:
+        ba.ba_set_tuning(ba.BA_KIND_DEGREE, None)
+    np.testing.assert_array_equal(got.cpu().numpy().astype(np.uint64), want)
