@@ -179,9 +179,14 @@ ba_status ba_check_status(const uint64_t *status_dev, void *stream);
  *                            n0 = 1 or NO_SELF_LOOPS) and for at most 65536 redraws.
  *                            Chains follow the array without rejection, so only the
  *                            node's own output changes.  Needs d <= 1024; combines with
- *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  A
- *                            degree count generates the targets chunk by chunk (2^27 edges,
- *                            2 GB of library scratch from its stream-ordered pool) and
+ *                            NO_SELF_LOOPS (a simple graph) but not with CRC_HASH.  For d a
+ *                            power of two <= 32 the repeats are found while the edges are
+ *                            generated and only the nodes with one are reworked (library
+ *                            scratch from the stream-ordered pool: 4 bytes per node listed,
+ *                            at most range/64 + 2^20 entries for an edge list and 2^25 for a
+ *                            degree count, which stores no edge); for other d a second pass
+ *                            reads the written output back, and a degree count generates
+ *                            the targets chunk by chunk (2^27 edges, 2 GB of scratch) and
  *                            counts every edge's final target.
  * The flags combine as stated.  Unknown flags, NO_SELF_LOOPS with n0 < 2, or
  * NO_PARALLEL_EDGES outside its limits give BA_ERR_INVALID_ARG. */

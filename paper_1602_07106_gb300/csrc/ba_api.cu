@@ -364,6 +364,48 @@ constexpr uint64_t kRejectCountChunk = 1ull << 27;
 static_assert(BA_VARIANT_CRC_HASH == kVariantCrc && BA_VARIANT_NO_SELF_LOOPS == kVariantNoLoop,
               "public variant flags and kernel policies disagree");
 
+// Section 4's graph without parallel edges through the fold (d a power of two <= 32): the
+// generate kernel with the detecting chunk flush, then the exact pass over the nodes it
+// listed.  Edge lists: one launch over the range, writing edge c at slot c - begin of out,
+// with a list of (range >> 6) + 2^20 entries at most; should more nodes be listed, the
+// exact pass takes every node instead.  Counting (out == nullptr): launches of at most
+// 2^25 nodes' edges, each with a list that holds all of its nodes, since the flush has
+// already counted the nodes it did not list.
+static ba_status fold_range(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0, uint64_t begin,
+                            uint64_t end, int64_t *out, uint64_t *counts, uint64_t node_limit,
+                            bool no_loops, cudaStream_t s) {
+  const uint64_t m0 = n0 > 0 ? n0 * (n0 - 1) / 2 : 0;
+  const uint64_t span = out ? end - begin : (1ull << 25) * d;
+  const uint64_t nodes = std::min(end - begin, span) / d + 2;  // nodes a launch can list
+  const uint64_t cap = out ? std::min<uint64_t>(nodes, ((end - begin) >> 6) + (1ull << 20)) : nodes;
+  Shape shape = shape_for(BA_KIND_GENERATE, end <= (1ull << 31));
+  shape.refill = 1;
+  StreamScratch list, count, counter;
+  ba_status st;
+  if ((st = list.alloc(cap * sizeof(uint32_t), s)) != BA_OK) return st;
+  if ((st = count.alloc(sizeof(unsigned long long), s)) != BA_OK) return st;
+  if ((st = counter.alloc(sizeof(unsigned long long), s)) != BA_OK) return st;
+  uint32_t *lst = static_cast<uint32_t *>(list.ptr);
+  unsigned long long *cnt = static_cast<unsigned long long *>(count.ptr);
+  for (uint64_t c0 = begin; c0 < end; c0 += span) {
+    const uint64_t c1 = std::min(end, c0 + span);
+    GraphDev gc = make_graph_dev(seed, n, d, n0, c0, c1);
+    gc.out_edge = c0 - begin;
+    const uint64_t lo = std::max(c0, m0);  // the launch's first node edge
+    const uint64_t q0 = lo < c1 ? (lo - m0) / d : 0;
+    const uint64_t q_hi = lo < c1 ? (c1 - 1 - m0) / d : 0;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    st = launch_generate_fold(gc, out, shape, static_cast<unsigned long long *>(counter.ptr), s,
+                              no_loops, lst, cnt, q0, cap, counts, node_limit);
+    if (st != BA_OK) return st;
+    if (lo >= c1) continue;  // seed-clique edges only: no node to finish
+    st = launch_reject_listed(gc, out, counts, node_limit, lst, cnt, cap, q0, q_hi, s, no_loops);
+    if (st != BA_OK) return st;
+  }
+  return BA_OK;
+}
+
 ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_t n0,
                                     uint64_t edge_begin, uint64_t edge_end, uint32_t variant,
                                     int64_t *out_dev, void *stream) {
@@ -379,6 +421,9 @@ ba_status ba_generate_edges_variant(uint64_t seed, uint64_t n, uint32_t d, uint6
     return BA_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((variant & BA_VARIANT_NO_PARALLEL_EDGES) && fold_supported(d))
+    return fold_range(seed, n, d, n0, edge_begin, edge_end, out_dev, nullptr, 0,
+                      (variant & BA_VARIANT_NO_SELF_LOOPS) != 0, s);
   const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
   Shape shape = shape_for(BA_KIND_GENERATE, edge_end <= (1ull << 31));
   shape.refill = 1;  // the variant draws run on the refill kernel only
@@ -431,6 +476,9 @@ ba_status ba_degree_count_variant(uint64_t seed, uint64_t n, uint32_t d, uint64_
   if (st != BA_OK) return st;
   const uint64_t a = std::max(edge_begin, g.m0);
   if (a >= edge_end) return BA_OK;
+  if (fold_supported(d))  // no edge stored: the fold counts as it generates
+    return fold_range(seed, n, d, n0, a, edge_end, nullptr, counts_dev, node_limit,
+                      (variant & BA_VARIANT_NO_SELF_LOOPS) != 0, s);
   const uint64_t chunk = std::min<uint64_t>(edge_end - a, kRejectCountChunk);
   StreamScratch pairs, counter;
   if ((st = pairs.alloc(chunk * 16, s)) != BA_OK) return st;

@@ -22,6 +22,15 @@ struct SchedParams {
   // is skipped and the lowest such slot is kept in *status (atomicMin)
   uint64_t out_cap;
   unsigned long long *status;
+  // fold launches only (ba_fold.cu): the nodes that the chunk flush hands on to the exact
+  // pass of section 4's rejection, as offsets from fold_q0 (at most fold_cap of them,
+  // *fold_count of them written), and, when counting, the counters below fold_limit
+  uint32_t *fold_list;
+  unsigned long long *fold_count;
+  uint64_t fold_q0;
+  uint64_t fold_cap;
+  unsigned long long *fold_counts;
+  uint64_t fold_limit;
 };
 
 // Graph table of a batched launch (device pointers).
@@ -93,6 +102,27 @@ ba_status launch_count_rejections(const GraphDev &g, const int64_t *pairs, uint6
 // every non-seed edge and both ends of every seed-clique edge (k_degree_init).
 ba_status launch_degree_sources(const GraphDev &g, uint64_t node_limit, uint64_t *counts,
                                 int accumulate, cudaStream_t stream);
+// ---- section 4's rejection folded into the generate kernel (ba_fold.cu), for d a power of
+// two in 2..32.  Generates edges [g.begin, g.end) with the array's targets (written to out,
+// or, with out == nullptr, counted: one per target below node_limit of a node the pass
+// settles) and lists in list[] (offsets from node q0, at most cap entries, the number at
+// *list_count, zeroed by the caller) every node that holds a repeated target or is cut by a
+// chunk; launch_reject_listed then finishes the listed nodes.  no_loops: the self-loop-free
+// draw.  counter: >= 8 bytes of device memory.
+bool fold_supported(uint32_t d);
+ba_status launch_generate_fold(const GraphDev &g, int64_t *out, const Shape &s,
+                               unsigned long long *counter, cudaStream_t stream, bool no_loops,
+                               uint32_t *list, unsigned long long *list_count, uint64_t q0,
+                               uint64_t cap, uint64_t *counts, uint64_t node_limit);
+// The exact pass of the rejection for the listed nodes only (ba_simple.cu): out == nullptr
+// counts final targets below node_limit (recomputing every target; the list must then hold
+// every listed node: list_cap >= the nodes q0..q_hi), else writes changed targets back
+// (and takes every node q0..q_hi when more than list_cap were listed).  q0, q_hi: the
+// nodes the list may name.
+ba_status launch_reject_listed(const GraphDev &g, int64_t *out, uint64_t *counts,
+                               uint64_t node_limit, const uint32_t *list,
+                               const unsigned long long *list_count, uint64_t list_cap,
+                               uint64_t q0, uint64_t q_hi, cudaStream_t stream, bool no_loops);
 // launch_generate with every output store checked against out_cap (edges): see SchedParams.
 ba_status launch_generate_checked(const GraphDev &g, int64_t *out, uint64_t out_cap,
                                   unsigned long long *status, const Shape &s,

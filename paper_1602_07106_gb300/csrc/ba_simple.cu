@@ -52,17 +52,22 @@ constexpr int kThreads = 256;
 constexpr int kGroup = 4;  // items per pass of a warp's loop
 constexpr uint32_t kNoKey = 0xffffffffu;
 
-// Warp items of npw consecutive nodes n0 + q, q in [q_lo, q_hi]: the W = npw * d edges
-// i0 + item * W + lane (lane < W), i0 = the first edge of node n0 + q_lo; lane = slot*d + j.
-// Count: `out` is scratch that the generate kernel has just filled with this range's edges
-// (the array's targets, as for the edge list); nothing is written back, and instead every
-// edge's final target below node_limit is counted (section 3's streaming analysis of this
-// graph: the sources are counted in closed form by the caller).
-template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
+// Warp items of npw nodes n0 + q: item x holds the nodes of index x*npw + slot of the
+// node sequence, lane = slot*d + j on edge m0 + q*d + j.  The sequence is q_lo..q_hi, or,
+// Listed, q_lo + list[0 .. *list_count) (the nodes a fold launch handed on, each once),
+// unless more than list_cap were handed on: then the list is incomplete and every node
+// q_lo..q_hi is taken (the fold wrote the array's targets, so that is the full pass).
+// Count: nothing is written back, and instead every edge's final target below node_limit
+// is counted (section 3's streaming analysis of this graph: the sources are counted in
+// closed form by the caller); the array's targets are read from `out`, scratch that the
+// generate kernel has just filled with this range's edges, or, Recompute, recomputed.
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count, bool Listed = false,
+          bool Recompute = false>
 __global__ void __launch_bounds__(kThreads)
 k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
                     unsigned long long *__restrict__ counts, uint64_t node_limit, uint64_t q_lo,
-                    uint64_t q_hi, uint32_t npw) {
+                    uint64_t q_hi, uint32_t npw, const uint32_t *__restrict__ list,
+                    const unsigned long long *__restrict__ list_count, uint64_t list_cap) {
   // per warp: the low 32 bits of each node's targets, written twice in a row (entries j
   // and j + d) so that lane j reads entry j + o for every offset o without a wrap; node s's
   // row starts at word s * (d + 64), so the lanes of one read hit distinct banks (d >= 2:
@@ -79,22 +84,38 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
   const uint32_t j = lane - slot * d;
   uint32_t *row = key_rows[threadIdx.x >> 5] + slot * (d + 64) + j;  // used by lanes < W
   const uint32_t half = d / 2;
-  const uint64_t i0 = g.m0 + q_lo * d;
-  const uint64_t items = (q_hi - q_lo) / npw + 1;
+  uint64_t nodes = q_hi - q_lo + 1;
+  bool use_list = false;
+  if constexpr (Listed) {
+    const uint64_t listed = *list_count;
+    if (listed <= list_cap) {
+      nodes = min(nodes, listed);
+      use_list = true;
+    }
+  }
+  const uint64_t items = (nodes + npw - 1) / npw;
   const uint64_t groups = (items + kGroup - 1) / kGroup;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kThreads / 32);
-  long long *const tgt = reinterpret_cast<long long *>(out) + 1;  // targets: stride 2
+  long long *const tgt =  // targets: stride 2 (no output when recomputing)
+      Recompute ? nullptr : reinterpret_cast<long long *>(out) + 1;
   for (uint64_t grp = static_cast<uint64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
        grp < groups; grp += warps) {
-    // kGroup consecutive items per pass of the loop: their loads in flight together
-    const uint64_t ib = i0 + grp * (kGroup * W) + lane;  // this lane's edge in the first
+    // This lane's node in item k of the group (q_lo + the sequence index; ~0 for none) and
+    // its edge there.
+    auto node_of = [&](int k) -> uint64_t {
+      const uint64_t x = (grp * kGroup + k) * npw + slot;
+      if (lane >= W || x >= nodes) return ~0ull;
+      return use_list ? q_lo + list[x] : q_lo + x;
+    };
+    auto edge_of = [&](uint64_t q) { return q == ~0ull ? ~0ull : g.m0 + q * d + j; };
+    // kGroup items per pass of the loop: their loads in flight together
     uint64_t t[kGroup];
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
-      const uint64_t ik = ib + k * W;
+      const uint64_t ik = edge_of(node_of(k));
       t[k] = 0;
-      if (lane < W && ik < g.end) {  // only the range's first node can start before it
-        if (ik >= g.begin)
+      if (ik < g.end) {  // only the range's first node can start before it
+        if (ik >= g.begin && !Recompute)
           t[k] = static_cast<uint64_t>(__ldcs(tgt + 2 * (g.out_edge + (ik - g.begin))));
         else
           t[k] = array_value<RT, HasSeed>(draw(static_cast<RT>(2 * ik + 1)), g, draw, l2m0);
@@ -109,7 +130,7 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
     uint32_t flags = 0;
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
-      const bool part = lane < W && ib + k * W < g.end;  // the edge matters to its node
+      const bool part = edge_of(node_of(k)) < g.end;  // the edge matters to its node
       const uint32_t key = static_cast<uint32_t>(t[k]);
       __syncwarp();
       if (lane < W) row[0] = row[d] = part ? key : kNoKey;
@@ -124,14 +145,13 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
     // Count: an edge of the range whose final target is a counted node adds one to it
     auto count = [&](uint64_t i, uint64_t target) {
       if constexpr (Count) {
-        if (lane < W && i < g.end && i >= g.begin && target < node_limit)
-          atomicAdd(counts + target, 1ull);
+        if (i < g.end && i >= g.begin && target < node_limit) atomicAdd(counts + target, 1ull);
       }
     };
     if (__ballot_sync(kAll, flags != 0) == 0) {
       if constexpr (Count) {
 #pragma unroll
-        for (int k = 0; k < kGroup; ++k) count(ib + k * W, t[k]);
+        for (int k = 0; k < kGroup; ++k) count(edge_of(node_of(k)), t[k]);
       }
       continue;
     }
@@ -140,19 +160,20 @@ k_reject_duplicates(const GraphDev g, int64_t *__restrict__ out,
 #pragma unroll 1
     for (int k = 0; k < kGroup; ++k) {
       uint32_t dups = __ballot_sync(kAll, (flags >> k) & 1u);
+      const uint64_t q_k = node_of(k);
+      const uint64_t i = edge_of(q_k);
       if (dups == 0) {
-        if constexpr (Count) count(ib + k * W, k == 0 ? t[0] : k == 1 ? t[1] : k == 2 ? t[2] : t[3]);
+        if constexpr (Count) count(i, k == 0 ? t[0] : k == 1 ? t[1] : k == 2 ? t[2] : t[3]);
         continue;
       }
-      const uint64_t i = ib + k * W;
-      const bool part = lane < W && i < g.end;
+      const bool part = i < g.end;
       const uint32_t parts = __ballot_sync(kAll, part);
       const uint64_t t_k = k == 0 ? t[0] : k == 1 ? t[1] : k == 2 ? t[2] : t[3];
       uint64_t acc = t_k;
       while (dups) {
         const uint32_t base = ((__ffs(dups) - 1) / d) * d;
         const uint32_t node_lanes = (d == 32 ? kAll : ((1u << d) - 1u)) << base;
-        const uint64_t node = g.n0 + q_lo + (grp * kGroup + k) * npw + base / d;
+        const uint64_t node = g.n0 + __shfl_sync(kAll, q_k, base);
         const uint64_t reach = NoLoop ? node : (g.n0 == 1 ? node : node + 1);
         for (uint32_t L = base + 1; L < base + d && ((parts >> L) & 1u); ++L) {
           const uint64_t iL = i - lane + L;
@@ -359,9 +380,33 @@ ba_status launch_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
   const uint64_t want = (groups + kBlock / 32 - 1) / (kBlock / 32);
   const int grid = static_cast<int>(std::min<uint64_t>(
       want, static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(std::max(per_sm, 1))));
-  kernel<<<grid, kBlock, 0, stream>>>(g, out, counts, node_limit, q_lo, q_hi, npw);
+  kernel<<<grid, kBlock, 0, stream>>>(g, out, counts, node_limit, q_lo, q_hi, npw, nullptr,
+                                      nullptr, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? BA_OK : cuda_fail(e, "k_reject_duplicates");
+}
+
+// The listed nodes only: the list's length is on the device, so the grid is the
+// persistent one and the warps stride over the items.
+template <class RT, bool HasSeed, class Draw, bool NoLoop, bool Count>
+ba_status launch_listed_t(const GraphDev &g, int64_t *out, unsigned long long *counts,
+                          uint64_t node_limit, uint64_t q_lo, uint64_t q_hi, uint32_t npw,
+                          const uint32_t *list, const unsigned long long *list_count,
+                          uint64_t list_cap, cudaStream_t stream) {
+  auto kernel = k_reject_duplicates<RT, HasSeed, Draw, NoLoop, Count, true, Count>;
+  constexpr int kBlock = kThreads;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  const uint64_t items = (q_hi - q_lo) / npw + 1;  // at most this many
+  const uint64_t groups = (items + kGroup - 1) / kGroup;
+  const uint64_t want = (groups + kBlock / 32 - 1) / (kBlock / 32);
+  const int grid = static_cast<int>(std::min<uint64_t>(
+      want, static_cast<uint64_t>(sm_count()) * static_cast<uint64_t>(std::max(per_sm, 1))));
+  kernel<<<grid, kBlock, 0, stream>>>(g, out, counts, node_limit, q_lo, q_hi, npw, list,
+                                      list_count, list_cap);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? BA_OK : cuda_fail(e, "k_reject_duplicates<listed>");
 }
 
 // The nodes with edges in [g.begin, g.end), then the launch for the draw family.
@@ -399,7 +444,41 @@ ba_status reject_range(const GraphDev &g, int64_t *out, unsigned long long *coun
              : launch_t<uint64_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, stream);
 }
 
+// The listed nodes of a fold launch, for the draw family (Count: the fold wrote nothing,
+// so the targets are recomputed).
+template <bool Count>
+ba_status reject_listed(const GraphDev &g, int64_t *out, unsigned long long *counts,
+                        uint64_t node_limit, const uint32_t *list,
+                        const unsigned long long *list_count, uint64_t list_cap, uint64_t q_lo,
+                        uint64_t q_hi, cudaStream_t stream, bool no_loops) {
+  const uint32_t npw = 32u / g.d;
+  const bool r32 = g.end <= (1ull << 31);
+  if (no_loops) {
+    using D = DrawVariant<false, true>;
+    return r32 ? launch_listed_t<uint32_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream)
+               : launch_listed_t<uint64_t, true, D, true, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream);
+  }
+  if (g.m0 > 0)
+    return r32 ? launch_listed_t<uint32_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream)
+               : launch_listed_t<uint64_t, true, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream);
+  return r32 ? launch_listed_t<uint32_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream)
+             : launch_listed_t<uint64_t, false, DrawPlain, false, Count>(g, out, counts, node_limit, q_lo, q_hi, npw, list, list_count, list_cap, stream);
+}
+
 }  // namespace
+
+ba_status launch_reject_listed(const GraphDev &g, int64_t *out, uint64_t *counts,
+                               uint64_t node_limit, const uint32_t *list,
+                               const unsigned long long *list_count, uint64_t list_cap,
+                               uint64_t q0, uint64_t q_hi, cudaStream_t stream, bool no_loops) {
+  if (g.d < 2 || g.d > 32 || q_hi < q0) return BA_ERR_INVALID_ARG;
+  if (out == nullptr)
+    return reject_listed<true>(g, nullptr, reinterpret_cast<unsigned long long *>(counts),
+                               node_limit, list, list_count, list_cap, q0, q_hi, stream,
+                               no_loops);
+  return reject_listed<false>(g, out, nullptr, 0, list, list_count, list_cap, q0, q_hi, stream,
+                              no_loops);
+}
 
 ba_status launch_reject_duplicates(const GraphDev &g, int64_t *out, cudaStream_t stream,
                                    bool no_loops) {

@@ -29,7 +29,8 @@ CASES = [(21, 20_000, 4, 0, False, 0, None), (22, 5_000, 16, 0, False, 37, -11),
          (23, 3_000, 32, 33, True, 0, None), (24, 4_000, 5, 6, False, 100, 15_000),
          (25, 100_000, 3, 1, False, 0, None), (26, 2_000, 32, 0, False, 0, None),
          (27, 30_000, 7, 8, True, 1_234, -77), (28, 50_000, 2, 2, True, 0, None),
-         (29, 3_000, 31, 0, False, 5, -3), (2**64 - 1, 9_000, 9, 0, False, 0, None)]
+         (29, 3_000, 31, 0, False, 5, -3), (2**64 - 1, 9_000, 9, 0, False, 0, None),
+         (32, 20_000, 16, 5, False, 3, -5), (33, 10_000, 8, 3, True, 0, None)]
 
 
 @pytest.mark.parametrize("seed,n,d,n0,no_loops,a,b", CASES)
@@ -190,5 +191,29 @@ def test_degree_count_64bit_positions(ba):
     want = oracle.degree_count_range_simple(seed, n, d, 0, False, a, b, 100_000)
     counts = torch.empty(100_000, dtype=torch.int64, device="cuda")
     ba.ba_degree_count_variant(seed, n, d, 0, a, b, 100_000, SIMPLE, counts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("no_loops,n0", [(False, 0), (True, 3)])
+def test_fold_launch_boundary(ba, no_loops, n0):
+    # d = 2: the fold generates 2^25 nodes' edges (2^26 edges) per launch, so this range is
+    # two launches, the second starting inside a node; the edges around the boundary and a
+    # degree count over the whole range match the oracle
+    seed, n, d = 41, 2**27, 2
+    a = 1_000_001
+    b = a + 2**26 + 20_000
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    out = torch.empty((b - a, 2), dtype=torch.int64, device="cuda")
+    ba.ba_generate_edges_variant(seed, n, d, n0, a, b, v, out)
+    torch.cuda.synchronize()
+    cut = a + 2**26
+    for lo, hi in [(a, a + 3_000), (cut - 5_000, cut + 5_001), (b - 3_000, b)]:
+        np.testing.assert_array_equal(out[lo - a:hi - a].cpu().numpy(),
+                                      opar.edges_range_simple(seed, n, d, n0, no_loops, lo, hi))
+    limit = 50_000
+    want = opar.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+    counts = torch.empty(limit, dtype=torch.int64, device="cuda")
+    ba.ba_degree_count_variant(seed, n, d, n0, a, b, limit, v, counts)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
