@@ -324,7 +324,7 @@ def cpu_baseline_leg(seconds_hint: float, sample_edges: int):
 
 # ---------------------------------------------------------------------- GPU arm --
 
-KERNEL_SOURCES = ("ba_device.cuh", "ba_draw.cuh", "ba_kernels.cu")
+KERNEL_SOURCES = ("ba_device.cuh", "ba_draw.cuh", "ba_refill.cuh", "ba_kernels.cu")
 
 
 def source_digest() -> str:
