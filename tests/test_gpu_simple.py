@@ -217,3 +217,24 @@ def test_fold_launch_boundary(ba, no_loops, n0):
     ba.ba_degree_count_variant(seed, n, d, n0, a, b, limit, v, counts)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("d,n0,no_loops", [(32, 40, False), (32, 40, True), (8, 6, True),
+                                          (4, 0, False)])
+def test_fold_64bit_positions_seeded(ba, d, n0, no_loops):
+    # the fold on 64-bit positions, with seed cliques whose edge count is not a multiple
+    # of d (m0 = 780 for n0 = 40: every chunk cuts a node), ranges that start and end
+    # inside nodes; edges and a degree count against the oracle
+    seed, n = 91, 2**30 // d * 4
+    m = oracle.num_edges(n, d, n0)
+    a, b = m - 150_001 - 2**32 // 3, m - 2**32 // 3 - 7
+    assert b > 2**31
+    v = SIMPLE | (NOLOOP if no_loops else 0)
+    np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b, v),
+                                  oracle.edges_range_simple(seed, n, d, n0, no_loops, a, b))
+    limit = 100_000
+    want = oracle.degree_count_range_simple(seed, n, d, n0, no_loops, a, b, limit)
+    counts = torch.empty(limit, dtype=torch.int64, device="cuda")
+    ba.ba_degree_count_variant(seed, n, d, n0, a, b, limit, v, counts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.uint64), want)
