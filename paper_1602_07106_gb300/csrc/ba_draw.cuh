@@ -75,6 +75,50 @@ __host__ __device__ constexpr size_t crc_table_smem(bool r32) {
   return static_cast<size_t>(crc_table_bytes(r32)) * 256u * sizeof(uint32_t);
 }
 
+// x mod r for a 64-bit x and 1 <= r < 2^32, exactly, without a 64-bit division: r is
+// normalised to d = r * 2^s in [2^31, 2^32) and x * 2^s (96 bits) reduced by two 2-by-1
+// division steps with the reciprocal v = floor((2^64 - 1) / d) - 2^32 (Moller & Granlund,
+// "Improved division by invariant integers", IEEE Trans. Computers 60(2), 2011, the
+// division of a two-word number by a normalised word).  Here d changes with every call,
+// so v comes from the hardware's approximate single-precision reciprocal (error of a few
+// 1e-7, so |v0 - v| < 2^12) made exact with integer arithmetic: the residual
+// e = 2^64 - d (2^32 + v0) gives the step k ~ e / d (in single precision: within one of
+// the exact step), and one unit step each way settles the largest v with e(v) >= 1.
+__device__ __forceinline__ uint32_t recip_word(uint32_t d) {
+  const float f = __uint2float_rn(d);
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  const float w = (y * 4294967296.0f - 1.0f) * 4294967296.0f;  // ~ v, in (0, 2^32]
+  const uint32_t v0 = __float2uint_rz(w);                        // saturates at 2^32 - 1
+  int64_t e = static_cast<int64_t>(0ull - (static_cast<uint64_t>(d) * v0 +
+                                           (static_cast<uint64_t>(d) << 32)));
+  const float ef = fmaf(__int2float_rn(static_cast<int32_t>(e >> 32)), 4294967296.0f,
+                        __uint2float_rn(static_cast<uint32_t>(e)));
+  const int32_t k = __float2int_rd(ef * y);
+  int64_t v = static_cast<int64_t>(v0) + k;
+  e -= static_cast<int64_t>(k) * static_cast<int64_t>(d);
+  if (e < 1) { --v; e += d; }
+  if (e > static_cast<int64_t>(d)) { ++v; e -= d; }
+  return static_cast<uint32_t>(v);
+}
+// (u1 * 2^32 + u0) mod d for u1 < d, d normalised, v = recip_word(d).
+__device__ __forceinline__ uint32_t rem_2by1(uint32_t u1, uint32_t u0, uint32_t d, uint32_t v) {
+  const uint64_t q = static_cast<uint64_t>(v) * u1 + (static_cast<uint64_t>(u1 + 1) << 32) + u0;
+  uint32_t r = u0 - static_cast<uint32_t>(q >> 32) * d;
+  if (r > static_cast<uint32_t>(q)) r += d;
+  if (r >= d) r -= d;
+  return r;
+}
+__device__ __forceinline__ uint32_t mod_64by32(uint64_t x, uint32_t r) {
+  const uint32_t s = __clz(r);
+  const uint32_t d = r << s;
+  const uint32_t v = recip_word(d);
+  const uint32_t x2 = s ? static_cast<uint32_t>(x >> (64 - s)) : 0u;
+  const uint64_t xs = x << s;
+  const uint32_t r1 = rem_2by1(x2, static_cast<uint32_t>(xs >> 32), d, v);
+  return rem_2by1(r1, static_cast<uint32_t>(xs), d, v) >> s;
+}
+
 template <bool Crc, bool NoLoop>
 struct DrawVariant {
   static constexpr bool kPlain = false;
@@ -142,7 +186,9 @@ struct DrawVariant {
   __device__ __forceinline__ RT operator()(RT r) const {
     const RT range = range_of<RT>(r);
     if constexpr (Crc) {
-      return static_cast<RT>(crc_bits<RT>(r) % static_cast<uint64_t>(range));
+      // Fig. 3's remainder; a range below 2^32 on the 32-bit path
+      if constexpr (sizeof(RT) == 4) return mod_64by32(crc_bits<RT>(r), range);
+      else return static_cast<RT>(crc_bits<RT>(r) % static_cast<uint64_t>(range));
     } else if constexpr (sizeof(RT) == 4) {
       // SplitMix64 bits of key r, multiply-high by the range (< 2^32), as in hash_r32_pre
       const uint64_t p = static_cast<uint64_t>(r) * kGamma;
