@@ -1,4 +1,5 @@
-// ba_kernels.cu -- the sm_103a kernels of libba and their launchers.
+// ba_kernels.cu -- the sm_103a kernels of libba and their launchers (the refill generate
+// kernel itself is defined in ba_refill.cuh, which ba_fold.cu shares).
 //
 // Generate (paper Fig. 1 over a range of edge IDs):
 //   k_generate_simple  one thread per edge, grid-stride; the parity baseline.
