@@ -45,7 +45,7 @@ struct FoldDetect {
     const IT n0 = static_cast<IT>(g.n0);
     const RT two_m0 = seed_limit<RT>(g.two_m0);
     const uint32_t delta = static_cast<uint32_t>(e0 - g.m0) & (D - 1);
-    int64_t *const dst = out + 2 * (g.out_edge + (e0 - g.begin));
+    int64_t *const dst = CountOnly ? nullptr : out + 2 * (g.out_edge + (e0 - g.begin));
     const bool first_chunk = e0 == g.begin;
     // rows [k_lo, k_hi) hold only edges of the chunk that belong to nodes (no seed-clique
     // edge, no lane outside the chunk): every node there is whole
