@@ -198,7 +198,7 @@ __device__ __forceinline__ void count_step(uint64_t &r, uint32_t &hoff, uint32_t
     asm volatile(
         "{\n\t"
         ".reg .pred p, h;\n\t"
-        ".reg .u32 t, fm, x;\n\t"
+        ".reg .u32 t, fm, x, rl, rh, nl, nh;\n\t"
         "cvt.u32.u64 t, %0;\n\t"
         "and.b32 t, t, 1;\n\t"
         "setp.eq.u32 p, t, 0;\n\t"
@@ -210,7 +210,11 @@ __device__ __forceinline__ void count_step(uint64_t &r, uint32_t &hoff, uint32_t
         "and.b32 x, fm, %3;\n\t"
         "popc.b32 x, x;\n\t"
         "add.u32 x, %1, x;\n\t"
-        "@p mad.wide.u32 %0, x, 2, %4;\n\t"
+        "mov.b64 {rl, rh}, %4;\n\t"
+        "mov.b64 {nl, nh}, %0;\n\t"
+        "@p mad.lo.cc.u32 nl, x, 2, rl;\n\t"
+        "@p addc.u32 nh, rh, 0;\n\t"
+        "mov.b64 %0, {nl, nh};\n\t"
         "popc.b32 x, fm;\n\t"
         "add.u32 %1, %1, x;\n\t"
         "}"
@@ -221,7 +225,7 @@ __device__ __forceinline__ void count_step(uint64_t &r, uint32_t &hoff, uint32_t
     asm volatile(
         "{\n\t"
         ".reg .pred p, h;\n\t"
-        ".reg .u32 t, fm, x;\n\t"
+        ".reg .u32 t, fm, x, rl, rh, nl, nh;\n\t"
         "cvt.u32.u64 t, %0;\n\t"
         "and.b32 t, t, 1;\n\t"
         "setp.eq.u32 p, t, 0;\n\t"
@@ -232,7 +236,11 @@ __device__ __forceinline__ void count_step(uint64_t &r, uint32_t &hoff, uint32_t
         "and.b32 x, fm, %3;\n\t"
         "popc.b32 x, x;\n\t"
         "add.u32 x, %1, x;\n\t"
-        "@p mad.wide.u32 %0, x, 2, %4;\n\t"
+        "mov.b64 {rl, rh}, %4;\n\t"
+        "mov.b64 {nl, nh}, %0;\n\t"
+        "@p mad.lo.cc.u32 nl, x, 2, rl;\n\t"
+        "@p addc.u32 nh, rh, 0;\n\t"
+        "mov.b64 %0, {nl, nh};\n\t"
         "popc.b32 x, fm;\n\t"
         "add.u32 %1, %1, x;\n\t"
         "}"
