@@ -114,9 +114,9 @@ def profile_case(args):
                                          ba.BA_VARIANT_NO_PARALLEL_EDGES, out, stream)
     elif args.profile == "degree":
         # a slice from the middle of the graph: its share of targets below 1e5 (~2%) is
-        # that of the whole graph, unlike a prefix
+        # that of the whole graph, unlike a prefix (the whole graph at 2^31 edges)
         counts = torch.empty(NODE_LIMIT, dtype=torch.int64, device="cuda")
-        a = 2**30
+        a = max(0, min(2**30, g.m - e))
         for _ in range(args.profile_reps):
             ba.ba_degree_count_range(g.seed, g.n, g.d, 0, a, a + e, NODE_LIMIT, counts, 0, stream)
     else:

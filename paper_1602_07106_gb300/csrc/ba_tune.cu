@@ -32,23 +32,34 @@ Cache &cache() {
   return c;
 }
 
-Shape default_shape(int kind) {
+// The shapes the autotuner settles on for a GB300 on the large workloads (2^31 edges on
+// 32-bit positions, 10^12 edges on 64-bit ones), so that a caller who never tunes gets them.
+// Occupancy decides most of it: the per-warp staging ring (4 KB on 32-bit positions, 8 KB on
+// 64-bit ones) and the degree count's hit buffers and shared bins must leave room for 24-48
+// resident warps per SM.
+Shape default_shape(int kind, bool r32) {
   Shape s;
+  s.refill = 1;
+  s.chains = 2;
   switch (kind) {
-    case BA_KIND_DEGREE:
-      s.block = 512; s.ctas_per_sm = 2; s.tile = 16384; s.refill = 1; s.hist_bins = 8192;
-      s.chains = 2;
+    case BA_KIND_DEGREE:  // 32 KB of shared bins; hit buffers of 32 (64) KB per 512 threads
+      s.block = 512; s.ctas_per_sm = r32 ? 4 : 2; s.tile = r32 ? 65536 : 16384;
+      s.hist_bins = 4096;
       break;
-    default:  // generate and batch
-      s.block = 256; s.ctas_per_sm = 4; s.tile = 65536; s.refill = 1; s.hist_bins = 0;
-      s.chains = 2;
+    case BA_KIND_BATCH:  // small graphs: shorter tiles, one chain per lane
+      s.block = 256; s.ctas_per_sm = 4; s.tile = r32 ? 16384 : 65536;
+      s.chains = r32 ? 1 : 2;
+      break;
+    default:  // generate: 16 warps of 4 KB rings, or 8 warps of 8 KB rings, per CTA
+      s.block = r32 ? 512 : 256; s.ctas_per_sm = 4; s.tile = 65536;
       break;
   }
   return s;
 }
 
+// Zero fields of an override take the 32-bit-position default.
 Shape from_public(const ba_tuning &t, int kind) {
-  Shape s = default_shape(kind);
+  Shape s = default_shape(kind, true);
   if (t.block > 0) s.block = t.block;
   if (t.ctas_per_sm > 0) s.ctas_per_sm = t.ctas_per_sm;
   if (t.tile > 0) s.tile = t.tile;
@@ -142,7 +153,7 @@ Shape shape_for(int kind, bool r32) {
   load_env_once(c);
   if (c.has_override[kind]) return c.override_shape[kind];
   if (c.has_tuned[kind][r32 ? 1 : 0]) return c.tuned[kind][r32 ? 1 : 0];
-  return default_shape(kind);
+  return default_shape(kind, r32);
 }
 
 ba_status shape_from_public(int kind, const ba_tuning *t, Shape *out) {
@@ -324,7 +335,7 @@ ba_status ba_tune(int32_t kind, uint64_t seed, uint64_t n, uint32_t d, uint64_t 
   }
   const GraphDev g = make_graph_dev(seed, n, d, n0, edge_begin, edge_end);
   float best_ms = 1e30f;
-  Shape best = default_shape(kind);
+  Shape best = default_shape(kind, r32);
   for (const Shape &cand : candidates(kind)) {
     float ms = 0;
     ba_status cst;

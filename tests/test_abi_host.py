@@ -103,6 +103,31 @@ def test_variant_argument_rules():
     ba.ba_degree_count_variant(1, 10, 2, 3, 0, 5, 0, 3, counts=None, stream=0)  # no counts
 
 
+def test_default_shapes_leave_room_for_resident_warps():
+    """The untuned shapes per position width: the staging rings (1024 positions per warp)
+    and the degree count's hit buffers (512 per warp) plus its 8-byte bins must let at
+    least 24 warps stay resident on an SM's 227 KB (8-byte rings allow 28 at most).  Asked
+    in a fresh process so that no tuner cache loaded by another test shadows the defaults."""
+    import json
+    import subprocess
+    import sys
+    code = ("import json; from paper_1602_07106_gb300 import ba; "
+            "print(json.dumps([ba.ba_get_tuning(k, e) for k in (0, 1, 2) for e in (2**31, 2**40)]))")
+    env = {k: v for k, v in os.environ.items() if k != "BA_TUNE_CACHE"}
+    out = subprocess.run([sys.executable, "-c", code], env=env, check=True, capture_output=True,
+                         text=True, cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    shapes = json.loads(out.stdout.strip().splitlines()[-1])
+    smem_sm = 227 * 1024
+    for (kind, pos_bytes), s in zip([(k, w) for k in (0, 1, 2) for w in (4, 8)], shapes):
+        warps = s["block"] // 32
+        per_cta = warps * 1024 * pos_bytes if kind != 1 else \
+            warps * 512 * pos_bytes + 8 * s["hist_bins"]
+        resident = min(s["ctas_per_sm"], smem_sm // per_cta) * warps
+        assert resident >= 24, (kind, pos_bytes, s)
+    g32, g64, d32, d64 = shapes[0], shapes[1], shapes[2], shapes[3]
+    assert d64["ctas_per_sm"] < d32["ctas_per_sm"] and g64["block"] < g32["block"]
+
+
 def test_tuning_overrides_validate_and_round_trip(tmp_path):
     default = ba.ba_get_tuning(ba.BA_KIND_GENERATE)
     assert default["block"] % 32 == 0 and default["tile"] & (default["tile"] - 1) == 0
