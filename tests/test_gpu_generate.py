@@ -182,6 +182,23 @@ def test_huge_seed_cliques(ba, seed, n, d, n0):
                                       oracle.edges_range(seed, n, d, n0, a, b))
 
 
+@pytest.mark.parametrize("seed,n,d,n0", [(8, 2**16 + 1, 2**15, 2**16),      # n0 d = 2^31, m = 2^31
+                                         (9, 2**15 + 10_001, 2**16, 2**15 + 1)])  # n0 d > 2^31
+def test_seeded_power_of_two_d_with_n0_d_at_2_31(ba, seed, n, d, n0):
+    # Seed cliques whose n0 d reaches 2^31 on 32-bit positions (m <= 2^31): node IDs near
+    # 2^16 with d = 2^15 and 2^16, chains that stop inside a clique of ~2^31 positions, and
+    # the last edge of a graph with exactly 2^31 edges; int64 and int32 pairs
+    m0 = n0 * (n0 - 1) // 2
+    m = ba.ba_num_edges(n, d, n0)
+    assert m <= 2**31
+    for a, b in [(m0 - 500, m0 + 700), (m - 700, m), ((m0 + m) // 2, (m0 + m) // 2 + 700)]:
+        want = oracle.edges_range(seed, n, d, n0, a, b)
+        np.testing.assert_array_equal(_gpu(ba, seed, n, d, n0, a, b), want)
+        out32 = torch.empty((b - a, 2), dtype=torch.int32, device="cuda")
+        ba.ba_generate_edges32(seed, n, d, n0, a, b, out32)
+        np.testing.assert_array_equal(out32.cpu().numpy().astype(np.int64), want)
+
+
 def test_concurrent_calls_from_host_threads(ba):
     # the library is called from several host threads at once, each on its own stream
     # (ctypes releases the GIL): every result is the one a lone call gives
