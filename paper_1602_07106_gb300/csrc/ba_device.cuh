@@ -149,9 +149,98 @@ __device__ __forceinline__ uint64_t hash_r64_pre_ptx(uint64_t seed_pre, uint64_t
       : "r"(rlo), "r"(rhi), "r"(slo), "r"(shi));
   return (static_cast<uint64_t>(ohi) << 32) | olo;
 }
+// The same two forms with the key and the range apart: the bits of key r, reduced into
+// 0..range-1 (section 4's self-loop-free draw keys on r but ranges over the earlier nodes'
+// edges only).  hash_rXX_pre_ptx(s, r) equals hash_rXX_keyed_ptx(s, r, r).
+__device__ __forceinline__ uint32_t hash_r32_keyed_ptx(uint64_t seed_pre, uint32_t r,
+                                                       uint32_t range) {
+  const uint32_t slo = static_cast<uint32_t>(seed_pre);
+  const uint32_t shi = static_cast<uint32_t>(seed_pre >> 32);
+  uint32_t out;
+  asm("{\n\t"
+      ".reg .u32 plo, phi, tlo, thi, xlo, xhi, zlo, zhi, q, c;\n\t"
+      "mul.lo.u32 plo, %1, 0x7F4A7C15;\n\t"
+      "mul.hi.u32 phi, %1, 0x7F4A7C15;\n\t"
+      "mad.lo.u32 phi, %1, 0x9E3779B9, phi;\n\t"
+      "shf.r.clamp.b32 tlo, plo, phi, 30;\n\t"
+      "shr.u32 thi, phi, 30;\n\t"
+      "lop3.b32 xlo, %2, plo, tlo, 0x96;\n\t"
+      "lop3.b32 xhi, %3, phi, thi, 0x96;\n\t"
+      "mul.lo.u32 zlo, xlo, 0x1CE4E5B9;\n\t"
+      "mul.hi.u32 zhi, xlo, 0x1CE4E5B9;\n\t"
+      "mad.lo.u32 zhi, xlo, 0xBF58476D, zhi;\n\t"
+      "mad.lo.u32 zhi, xhi, 0x1CE4E5B9, zhi;\n\t"
+      "shf.r.clamp.b32 tlo, zlo, zhi, 27;\n\t"
+      "shr.u32 thi, zhi, 27;\n\t"
+      "xor.b32 xlo, zlo, tlo;\n\t"
+      "xor.b32 xhi, zhi, thi;\n\t"
+      "mul.lo.u32 zlo, xlo, 0x133111EB;\n\t"
+      "mul.hi.u32 zhi, xlo, 0x133111EB;\n\t"
+      "mad.lo.u32 zhi, xlo, 0x94D049BB, zhi;\n\t"
+      "mad.lo.u32 zhi, xhi, 0x133111EB, zhi;\n\t"
+      "shf.r.clamp.b32 tlo, zlo, zhi, 31;\n\t"
+      "shr.u32 thi, zhi, 31;\n\t"
+      "xor.b32 zlo, zlo, tlo;\n\t"
+      "xor.b32 zhi, zhi, thi;\n\t"
+      "mul.hi.u32 q, zlo, %4;\n\t"                 // floor(z * range / 2^64)
+      "mad.lo.cc.u32 c, zhi, %4, q;\n\t"
+      "madc.hi.u32 %0, zhi, %4, 0;\n\t"
+      "}"
+      : "=r"(out)
+      : "r"(r), "r"(slo), "r"(shi), "r"(range));
+  return out;
+}
+__device__ __forceinline__ uint64_t hash_r64_keyed_ptx(uint64_t seed_pre, uint64_t r,
+                                                       uint64_t range) {
+  const uint32_t slo = static_cast<uint32_t>(seed_pre);
+  const uint32_t shi = static_cast<uint32_t>(seed_pre >> 32);
+  const uint32_t rlo = static_cast<uint32_t>(r);
+  const uint32_t rhi = static_cast<uint32_t>(r >> 32);
+  const uint32_t glo = static_cast<uint32_t>(range);
+  const uint32_t ghi = static_cast<uint32_t>(range >> 32);
+  uint32_t olo, ohi;
+  asm("{\n\t"
+      ".reg .u32 plo, phi, tlo, thi, xlo, xhi, zlo, zhi, a0, m1lo, m1hi, s0, s1, s2;\n\t"
+      "mul.lo.u32 plo, %2, 0x7F4A7C15;\n\t"
+      "mul.hi.u32 phi, %2, 0x7F4A7C15;\n\t"
+      "mad.lo.u32 phi, %2, 0x9E3779B9, phi;\n\t"
+      "mad.lo.u32 phi, %3, 0x7F4A7C15, phi;\n\t"
+      "shf.r.clamp.b32 tlo, plo, phi, 30;\n\t"
+      "shr.u32 thi, phi, 30;\n\t"
+      "lop3.b32 xlo, %4, plo, tlo, 0x96;\n\t"
+      "lop3.b32 xhi, %5, phi, thi, 0x96;\n\t"
+      "mul.lo.u32 zlo, xlo, 0x1CE4E5B9;\n\t"
+      "mul.hi.u32 zhi, xlo, 0x1CE4E5B9;\n\t"
+      "mad.lo.u32 zhi, xlo, 0xBF58476D, zhi;\n\t"
+      "mad.lo.u32 zhi, xhi, 0x1CE4E5B9, zhi;\n\t"
+      "shf.r.clamp.b32 tlo, zlo, zhi, 27;\n\t"
+      "shr.u32 thi, zhi, 27;\n\t"
+      "xor.b32 xlo, zlo, tlo;\n\t"
+      "xor.b32 xhi, zhi, thi;\n\t"
+      "mul.lo.u32 zlo, xlo, 0x133111EB;\n\t"
+      "mul.hi.u32 zhi, xlo, 0x133111EB;\n\t"
+      "mad.lo.u32 zhi, xlo, 0x94D049BB, zhi;\n\t"
+      "mad.lo.u32 zhi, xhi, 0x133111EB, zhi;\n\t"
+      "shf.r.clamp.b32 tlo, zlo, zhi, 31;\n\t"
+      "shr.u32 thi, zhi, 31;\n\t"
+      "xor.b32 zlo, zlo, tlo;\n\t"
+      "xor.b32 zhi, zhi, thi;\n\t"
+      "mul.hi.u32 a0, zlo, %6;\n\t"                // floor(z * range / 2^64) on halves
+      "mad.lo.cc.u32 m1lo, zhi, %6, a0;\n\t"
+      "madc.hi.u32 m1hi, zhi, %6, 0;\n\t"
+      "mad.lo.cc.u32 s0, zlo, %7, m1lo;\n\t"
+      "madc.hi.cc.u32 s1, zlo, %7, m1hi;\n\t"
+      "addc.u32 s2, 0, 0;\n\t"
+      "mad.lo.cc.u32 %0, zhi, %7, s1;\n\t"
+      "madc.hi.u32 %1, zhi, %7, s2;\n\t"
+      "}"
+      : "=r"(olo), "=r"(ohi)
+      : "r"(rlo), "r"(rhi), "r"(slo), "r"(shi), "r"(glo), "r"(ghi));
+  return (static_cast<uint64_t>(ohi) << 32) | olo;
+}
 static_assert(kGamma == 0x9E3779B97F4A7C15ull && kMixA == 0xBF58476D1CE4E5B9ull &&
                   kMixB == 0x94D049BB133111EBull,
-              "hash_r32_pre_ptx and hash_r64_pre_ptx spell these constants out");
+              "the PTX forms of the hash spell these constants out");
 
 __device__ __forceinline__ uint64_t hash_r64_pre(uint64_t seed_pre, uint64_t r) {
   const uint64_t p = r * kGamma;

@@ -190,19 +190,10 @@ struct DrawVariant {
       if constexpr (sizeof(RT) == 4) return mod_64by32(crc_bits<RT>(r), range);
       else return static_cast<RT>(crc_bits<RT>(r) % static_cast<uint64_t>(range));
     } else if constexpr (sizeof(RT) == 4) {
-      // SplitMix64 bits of key r, multiply-high by the range (< 2^32), as in hash_r32_pre
-      const uint64_t p = static_cast<uint64_t>(r) * kGamma;
-      uint64_t z = (spre ^ p ^ (p >> 30)) * kMixA;
-      z = (z ^ (z >> 27)) * kMixB;
-      z ^= z >> 31;
-      const uint32_t t = __umulhi(static_cast<uint32_t>(z), range);
-      return static_cast<uint32_t>((static_cast<uint64_t>(static_cast<uint32_t>(z >> 32)) * range + t) >> 32);
+      // SplitMix64 bits of key r, multiply-high by the range (< 2^32)
+      return hash_r32_keyed_ptx(spre, r, range);
     } else {
-      const uint64_t p = r * kGamma;
-      uint64_t z = (spre ^ p ^ (p >> 30)) * kMixA;
-      z = (z ^ (z >> 27)) * kMixB;
-      z ^= z >> 31;
-      return __umul64hi(z, range);
+      return hash_r64_keyed_ptx(spre, r, range);
     }
   }
 };
