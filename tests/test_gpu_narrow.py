@@ -47,6 +47,21 @@ def test_int32_output_does_not_depend_on_shape(ba, shape):
         ba.ba_set_tuning(ba.BA_KIND_GENERATE, None)
 
 
+@pytest.mark.parametrize("seed,n,d,a,b", [(41, 10**6, 16, 3, 3_000_000),   # d = 2^4
+                                           (43, 10**6, 12, 0, 2_500_001)])  # d not 2^l
+def test_int32_output_8_byte_aligned_only(ba, seed, n, d, a, b):
+    # The int32 entry point asks only for 8-byte alignment: an output 8 bytes past a
+    # 16-byte boundary gives the same edges as an aligned one, and the oracle's.
+    want = opar.edges_range(seed, n, d, 0, a, b)
+    buf = torch.full((b - a + 1, 2), -1, dtype=torch.int32, device="cuda")
+    for off in (0, 1):                      # byte offset 0 or 8 from a 16-byte boundary
+        assert (buf.data_ptr() + 8 * off) % 16 == 8 * off
+        view = buf[off:off + b - a]
+        ba.ba_generate_edges32(seed, n, d, 0, a, b, view)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(view.cpu().numpy().astype(np.int64), want)
+
+
 def test_int32_equals_int64_on_the_large_workload(ba):
     g = W.PLAIN_LARGE
     half = 2**30
