@@ -80,10 +80,13 @@ __host__ __device__ constexpr size_t crc_table_smem(bool r32) {
 // division steps with the reciprocal v = floor((2^64 - 1) / d) - 2^32 (Moller & Granlund,
 // "Improved division by invariant integers", IEEE Trans. Computers 60(2), 2011, the
 // division of a two-word number by a normalised word).  Here d changes with every call,
-// so v comes from the hardware's approximate single-precision reciprocal (error of a few
-// 1e-7, so |v0 - v| < 2^12) made exact with integer arithmetic: the residual
-// e = 2^64 - d (2^32 + v0) gives the step k ~ e / d (in single precision: within one of
-// the exact step), and one unit step each way settles the largest v with e(v) >= 1.
+// so v comes from the hardware's approximate single-precision reciprocal (relative error
+// below 2^-23, so |v0 - v| < 2^11) made exact with integer arithmetic.  v is the largest
+// value with residual e(v) = 2^64 - d (2^32 + v) >= 1, and then e(v) <= d.  From
+// e0 = e(v0) the exact step is k* = v - v0 = floor((e0 - 1) / d); e0 / d in single
+// precision is within 2^-11 of the real quotient, so rounding e0 / d - 2^-8 down gives
+// k* or k* - 1, never more: after the step 1 <= e <= 2d, and one compare settles it.
+// (Checked against floor((2^64 - 1) / d) - 2^32 for every d in [2^31, 2^32) on a GB300.)
 __device__ __forceinline__ uint32_t recip_word(uint32_t d) {
   const float f = __uint2float_rn(d);
   float y;
@@ -94,12 +97,9 @@ __device__ __forceinline__ uint32_t recip_word(uint32_t d) {
                                            (static_cast<uint64_t>(d) << 32)));
   const float ef = fmaf(__int2float_rn(static_cast<int32_t>(e >> 32)), 4294967296.0f,
                         __uint2float_rn(static_cast<uint32_t>(e)));
-  const int32_t k = __float2int_rd(ef * y);
-  int64_t v = static_cast<int64_t>(v0) + k;
-  e -= static_cast<int64_t>(k) * static_cast<int64_t>(d);
-  if (e < 1) { --v; e += d; }
-  if (e > static_cast<int64_t>(d)) { ++v; e -= d; }
-  return static_cast<uint32_t>(v);
+  const int32_t k = __float2int_rd(fmaf(ef, y, -0.00390625f));  // k* or k* - 1
+  e -= static_cast<int64_t>(k) * static_cast<int64_t>(d);       // 1 <= e <= 2d
+  return v0 + static_cast<uint32_t>(k) + (e > static_cast<int64_t>(d) ? 1u : 0u);
 }
 // (u1 * 2^32 + u0) mod d for u1 < d, d normalised, v = recip_word(d).
 __device__ __forceinline__ uint32_t rem_2by1(uint32_t u1, uint32_t u0, uint32_t d, uint32_t v) {
