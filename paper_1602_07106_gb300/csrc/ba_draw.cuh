@@ -113,10 +113,13 @@ __device__ __forceinline__ uint32_t mod_64by32(uint64_t x, uint32_t r) {
   const uint32_t s = __clz(r);
   const uint32_t d = r << s;
   const uint32_t v = recip_word(d);
-  const uint32_t x2 = s ? static_cast<uint32_t>(x >> (64 - s)) : 0u;
-  const uint64_t xs = x << s;
-  const uint32_t r1 = rem_2by1(x2, static_cast<uint32_t>(xs >> 32), d, v);
-  return rem_2by1(r1, static_cast<uint32_t>(xs), d, v) >> s;
+  // the three words of x * 2^s by funnel shifts (s <= 31; for s = 0 the top word is 0)
+  const uint32_t xlo = static_cast<uint32_t>(x);
+  const uint32_t xhi = static_cast<uint32_t>(x >> 32);
+  const uint32_t x2 = __funnelshift_lc(xhi, 0u, s);
+  const uint32_t x1 = __funnelshift_lc(xlo, xhi, s);
+  const uint32_t r1 = rem_2by1(x2, x1, d, v);
+  return rem_2by1(r1, xlo << s, d, v) >> s;
 }
 
 template <bool Crc, bool NoLoop>
