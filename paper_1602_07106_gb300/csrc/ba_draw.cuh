@@ -86,7 +86,7 @@ __host__ __device__ constexpr size_t crc_table_smem(bool r32) {
 // e0 = e(v0) the exact step is k* = v - v0 = floor((e0 - 1) / d); e0 / d in single
 // precision is within 2^-11 of the real quotient, so rounding e0 / d - 2^-8 down gives
 // k* or k* - 1, never more: after the step 1 <= e <= 2d, and one compare settles it.
-// (Checked against floor((2^64 - 1) / d) - 2^32 for every d in [2^31, 2^32) on a GB300.)
+// (A device test checks it against floor((2^64 - 1) / d) - 2^32 for every d in [2^31, 2^32).)
 __device__ __forceinline__ uint32_t recip_word(uint32_t d) {
   const float f = __uint2float_rn(d);
   float y;
