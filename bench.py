@@ -70,9 +70,11 @@ def parse_args():
 
 
 def profile_case(args):
-    """A few launches of one kernel on a small slice of the large workload: edges
+    """A few launches of one kernel on a slice of the large workload: edges
     [0, profile_edges) of n = 2^27, d = 16, seed 42 (1 GB of output at the default 2^26,
-    larger than L2), for ncu."""
+    larger than L2), for ncu.  --profile-edges 2147483648 gives the benchmark's own
+    2^31-edge launch (its 65536-edge tiles; for generate, whose output is then 34.4 GB,
+    only counters that ncu takes in one pass)."""
     import torch
 
     from paper_1602_07106_gb300 import build as ba_build
